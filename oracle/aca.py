@@ -1,0 +1,90 @@
+"""Partially pivoted adaptive cross approximation (ACA), fp64 oracle.
+
+§3.6 (the ACA form K_{t,s} ~ U V^* = K_{t,sigma} (K_{tau,sigma})^{-1} K_{tau,s}
+and its stopping rule ||u_p||_2 ||v_p||_2 <= eps ||K^(p)||_F).  The paper names
+only the rule; the steps below are Bebendorf's partially pivoted ACA in the
+reading this build fixes (both the oracle and the GPU library follow it):
+
+1. start with the first row position of I;
+2. residual row  r = K(I[i], J) - sum_{l<k} u_l[i] v_l   (l in order);
+3. column pivot j = argmax over unused columns of |r_j| (ties: smallest
+   position); if that maximum is 0, the row is spent: take the next unused
+   row in position order and go to 2 (stop if none is left);
+4. v = r / r_j; residual column u = K(I, J[j]) - sum_{l<k} v_l[j] u_l;
+5. ||S_k||_F^2 = ||S_{k-1}||_F^2 + 2 sum_{l<k} (u_l . u)(v_l . v) + |u|^2 |v|^2;
+6. accept the pivot (i, j); stop if |u| |v| <= eps ||S_k||_F;
+7. next row = argmax over unused rows of |u_i| (ties: smallest position; if
+   the maximum is 0, the next unused row in position order);
+8. the rank never exceeds min(|I|, |J|); an empty I or J gives rank 0.
+"""
+
+import math
+
+import numpy as np
+
+from . import kernels
+
+
+def aca_entries(row, col, nI, nJ, eps):
+    """ACA of an abstract nI x nJ matrix given by row(i) -> (nJ,) and
+    col(j) -> (nI,).  Returns (row positions, column positions, U, V) with
+    A ~ U V^T, U of shape (nI, k) and V of shape (nJ, k)."""
+    us, vs, rows, cols = [], [], [], []
+    if nI == 0 or nJ == 0:
+        return rows, cols, np.zeros((nI, 0)), np.zeros((nJ, 0))
+    row_used = np.zeros(nI, dtype=bool)
+    col_used = np.zeros(nJ, dtype=bool)
+    S2 = 0.0
+    i = 0
+    kmax = min(nI, nJ)
+    while len(rows) < kmax:
+        r = np.array(row(i), dtype=np.float64)
+        for l in range(len(us)):
+            r = r - us[l][i] * vs[l]
+        row_used[i] = True
+        a = np.abs(r)
+        a[col_used] = -1.0
+        j = int(np.argmax(a))
+        if a[j] <= 0.0:
+            free = np.flatnonzero(~row_used)
+            if free.size == 0:
+                break
+            i = int(free[0])
+            continue
+        v = r / r[j]
+        u = np.array(col(j), dtype=np.float64)
+        for l in range(len(us)):
+            u = u - vs[l][j] * us[l]
+        col_used[j] = True
+        uu = float(np.dot(u, u))
+        vv = float(np.dot(v, v))
+        cross = 0.0
+        for l in range(len(us)):
+            cross += float(np.dot(us[l], u)) * float(np.dot(vs[l], v))
+        S2 = S2 + 2.0 * cross + uu * vv
+        us.append(u)
+        vs.append(v)
+        rows.append(i)
+        cols.append(j)
+        if math.sqrt(uu) * math.sqrt(vv) <= eps * math.sqrt(max(S2, 0.0)):
+            break
+        a = np.abs(u)
+        a[row_used] = -1.0
+        i = int(np.argmax(a))
+        if a[i] <= 0.0:
+            free = np.flatnonzero(~row_used)
+            if free.size == 0:
+                break
+            i = int(free[0])
+    U = np.stack(us, axis=1) if us else np.zeros((nI, 0))
+    V = np.stack(vs, axis=1) if vs else np.zeros((nJ, 0))
+    return rows, cols, U, V
+
+
+def aca(kind, P, I, J, eps, param=0.1):
+    """ACA of the kernel block K_{I,J} (I, J global point indices)."""
+    I = np.asarray(I, dtype=np.int64)
+    J = np.asarray(J, dtype=np.int64)
+    return aca_entries(lambda i: kernels.block(kind, P, I[i:i + 1], J, param)[0],
+                       lambda j: kernels.block(kind, P, I, J[j:j + 1], param)[:, 0],
+                       I.size, J.size, eps)

@@ -1,0 +1,45 @@
+"""Seeded synthetic inputs shaped like the paper's experiments.
+
+This module holds random-number generation only, none of the method's
+arithmetic; the tests and the benchmark hand its arrays both to the CUDA
+library and to the FP64 oracle.
+
+The paper's MVP experiments draw N points i.i.d. uniform in [-1, 1]^d (§6.1.1
+for 2D, §6.2.1 for 3D) and random charge vectors q (averaged over 5 draws).
+Here: NumPy PCG64 streams; points U[lo, hi]^d, right-hand sides N(0, 1).
+Seeds: points 1000 + workload number, right-hand sides 2000 + workload number,
+instance k of the batched workload 3000 + k.
+"""
+
+import numpy as np
+
+#: Named workloads (sizes, kernel, tolerance) of the benchmarked configurations.
+WORKLOADS = {
+    # 2D log r, N = 4096, quadtree with leaves of <= 64 points on average (kappa 3)
+    "c1_2d_log_n4096": dict(number=1, N=4096, d=2, kernel="log2d", n_max=64, eps=1e-8, nrhs=1),
+    # 3D 1/r, N = 262144, octree kappa 4
+    "c2_3d_invr_n262144": dict(number=2, N=262144, d=3, kernel="invr", n_max=64, eps=1e-6, nrhs=1),
+    "c2_3d_invr_n262144_eps1e-9": dict(number=2, N=262144, d=3, kernel="invr", n_max=64,
+                                        eps=1e-9, nrhs=1),
+    # 2D log r, N = 2^20, kappa 7, 64 right-hand sides
+    "c3_2d_log_n1048576": dict(number=3, N=1 << 20, d=2, kernel="log2d", n_max=64, eps=1e-10,
+                                nrhs=64),
+}
+
+
+def points(N, d, seed, lo=-1.0, hi=1.0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=(N, d))
+
+
+def rhs(N, nrhs, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q = rng.standard_normal(size=(nrhs, N)).T.copy()   # column-major N x nrhs
+    return q[:, 0].copy() if nrhs == 1 else q
+
+
+def workload(name):
+    w = dict(WORKLOADS[name])
+    w["points"] = points(w["N"], w["d"], 1000 + w["number"])
+    w["q"] = rhs(w["N"], w["nrhs"], 2000 + w["number"])
+    return w
