@@ -1,0 +1,316 @@
+"""Benchmark of the H2*(b+t) matrix-vector product on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--storage f64|f32] [--variant h2star|h2plush|h2sqrt]
+
+A step is one full MVP (gather, P2M, M2M, M2L far + vertex-sharing, L2L, L2P
+with the near field evaluated on the fly, scatter) on the default workload:
+3D 1/r, N = 262144 points uniform in [-1, 1]^3, octree with leaves of <= 64
+points on average (kappa 4), NCA tolerance 1e-6, one N(0, 1) right-hand side,
+fp64.  The operators (GBs) are larger than the 129 MB L2, so no flush is
+needed between steps.  Prints one JSON line (rank 0).
+
+--impl reference times the FP64 CPU oracle (exact product, sampled rows) on
+the host cores instead.  Under torchrun each rank runs an independent replica
+(no collective on the data path); value is the sum over ranks.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H2* MVP points·RHS/s and % HBM roofline; GMRES solve p50/p99 latency"
+UNIT = "points*RHS/s"
+KERNEL_NAMES = {"log2d": "log r (2D)", "invr": "1/r (3D)", "imq": "inverse multiquadric",
+                "matern12": "exp(-r)"}
+VARIANT_NAMES = {"h2star": "H2*(b+t)", "h2plush": "(H2+H)*", "h2sqrt": "H2_sqrt(d)(b)"}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- oracle legs
+def oracle_rows_child(workload, seconds):
+    """Runs in a fresh single-threaded process: exact rows of K q by the oracle."""
+    from oracle import dense
+    from paper_2309_14085_gb300 import inputs
+    w = inputs.workload(workload)
+    P, q = w["points"], w["q"]
+    rng = np.random.default_rng(0)
+    rows, t_used = 0, 0.0
+    chunk = 16
+    while t_used < seconds:
+        idx = rng.choice(P.shape[0], chunk, replace=False)
+        t0 = time.perf_counter()
+        dense.rows(w["kernel"], P, q, idx, chunk=chunk)
+        t_used += time.perf_counter() - t0
+        rows += chunk
+    nrhs = w["nrhs"]
+    print(json.dumps({"rows": rows, "seconds": t_used, "value": rows * nrhs / t_used}))
+
+
+def run_oracle_rows(workload, seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", workload,
+                        str(seconds)], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                       env=env, timeout=600)
+    if p.returncode != 0:
+        raise RuntimeError("oracle child failed: " + p.stderr[-2000:])
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    r["cores"] = 1
+    r["sample"] = (f"{r['rows']} exact rows of K q (dense definition, oracle.dense.rows) of "
+                   f"the same workload, {r['seconds']:.1f} s single-threaded")
+    return r
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"h2_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+def bench_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2309_14085_gb300 import H2Matrix, inputs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    w = inputs.workload(args.workload)
+    N, nrhs = w["N"], w["nrhs"]
+    t0 = time.perf_counter()
+    A = H2Matrix(w["points"], w["kernel"], leaf_size=w["n_max"], tol=w["eps"],
+                 variant=args.variant, storage=args.storage)
+    build_s = time.perf_counter() - t0
+    info = A.info()
+    q = torch.tensor(w["q"].reshape(N, nrhs), dtype=torch.float64, device=dev)
+    Xc = q.t().contiguous().t()
+    Y = torch.empty((nrhs, N), dtype=torch.float64, device=dev).t()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        A.matvec(Xc, out=Y)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    A.profile(True)
+    clocks = Clocks(dev.index)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    stages, calls, launches = A.stage_times()
+    A.profile(False)
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * N * nrhs / (ms_step / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    hq = torch.tensor(w["q"].reshape(N, nrhs).T.copy(), dtype=torch.float64).pin_memory()
+    hy = torch.empty((nrhs, N), dtype=torch.float64).pin_memory()
+    dq = torch.empty((nrhs, N), dtype=torch.float64, device=dev)
+    dy = torch.empty((nrhs, N), dtype=torch.float64, device=dev)
+    e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        dq.copy_(hq, non_blocking=True)
+        A.matvec(dq.t(), out=dy.t())
+        hy.copy_(dy, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e_steps):
+        dq.copy_(hq, non_blocking=True)
+        A.matvec(dq.t(), out=dy.t())
+        hy.copy_(dy, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+
+    # roofline of the dominant kernel
+    per = {k: v / max(calls, 1) for k, v in stages.items()}
+    dom = max(per, key=per.get)
+    ts = 8 if args.storage == "f64" else 4
+    hbm, how = _peaks()
+    roof = {"kernel": dom, "stage_ms": {k: round(v, 4) for k, v in per.items()}}
+    if dom == "m2l":
+        alg = info["bytes_m2l"] + (info["m2l_src_coeffs"] + info["m2l_dst_coeffs"]) * ts
+        ach = alg / (per["m2l"] / 1e3) / 1e9
+        roof.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s",
+                    frac=round(ach / hbm, 4), traffic=None, alg_bytes=alg,
+                    peak_source=f"{how} hbm_gbs")
+    else:
+        # near field on the fly: kernel evaluations against the HBM-free ALU bound
+        alg = info["N"] * info["d"] * ts + 2 * info["N"] * ts + 2 * info["vlen"] * ts + \
+            info["bytes_basis"]
+        ach = alg / (per[dom] / 1e3) / 1e9
+        roof.update(bound="alu", achieved=round(ach, 1), peak=hbm, unit="GB/s",
+                    frac=round(ach / hbm, 4), traffic=None, alg_bytes=alg,
+                    near_evals_per_s=round(info["near_evals"] / (per[dom] / 1e3), 1),
+                    peak_source=f"{how} hbm_gbs (bytes of the leaf stage; it is ALU-bound)")
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.storage == "f64" else "f32",
+        "data": "synthetic (seeded uniform points in [-1,1]^d, N(0,1) right-hand sides)",
+        "config": {"workload": args.workload, "N": N, "d": w["d"],
+                   "kernel": KERNEL_NAMES[w["kernel"]], "leaf_size": w["n_max"],
+                   "kappa": info["kappa"], "eps": w["eps"], "variant": VARIANT_NAMES[args.variant],
+                   "storage": args.storage, "nrhs": nrhs,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "operators larger than L2 (no flush)",
+                   "build_seconds": round(build_s, 2),
+                   "device_bytes": info["bytes_device"],
+                   "ranks": info["ranks"]},
+        "clocks": clk,
+        "e2e": {"value": world * N * nrhs / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": N * nrhs * 8, "d2h_bytes_per_step": N * nrhs * 8},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+    }
+    return out, w
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2_3d_invr_n262144")
+    ap.add_argument("--storage", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--variant", default="h2star", choices=list(VARIANT_NAMES))
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--oracle-child", nargs=2, default=None)
+    args = ap.parse_args()
+    if args.oracle_child:
+        oracle_rows_child(args.oracle_child[0], float(args.oracle_child[1]))
+        return
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_2309_14085_gb300 import inputs
+        w = inputs.workload(args.workload)
+        per_step = max(1.0, min(args.cpu_seconds, 60.0 / max(args.steps + args.warmup, 1)))
+        vals = []
+        r = None
+        for i in range(args.warmup + args.steps):
+            r = run_oracle_rows(args.workload, per_step)
+            if i >= args.warmup:
+                vals.append(r["value"])
+        value = float(np.median(vals))
+        out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 * w["N"] * w["nrhs"] / value, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": args.workload, "N": w["N"], "d": w["d"],
+                          "kernel": KERNEL_NAMES[w["kernel"]], "eps": w["eps"]},
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": r["sample"]},
+               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out, w = bench_ours(args, rank, world)
+    if rank == 0:
+        cb = run_oracle_rows(args.workload, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],
+                               "kind": "oracle", "sample": cb["sample"]}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * h2star.h -- C ABI of the GB300 (sm_103a) library for the algebraic H2* fast
+ * matrix-vector product of Khan & Ambikasaran, "New algebraic fast algorithms
+ * for N-body problems in two and three dimensions" (arXiv 2309.14085).
+ *
+ * The library compresses a kernel matrix K(i,j) = G(|x_i - x_j|) over N points
+ * in d = 2 or 3 dimensions (same sources and targets) into
+ *   - H2*(b+t)      (§5.1): far-field clusters compressed by B2T NCA (Algorithm 1)
+ *                           and vertex-sharing clusters by T2B NCA (Algorithm 2),
+ *                           two independent nested bases;
+ *   - (H2+H)*       (§5.2): the same far field plus one ACA per vertex-sharing
+ *                           pair (Algorithms 3 and 4);
+ *   - H2_sqrt(d)(b) (App. A): standard far-field H2, one basis from B2T NCA;
+ * and applies it on the GPU (upward pass, coupling products, downward pass and
+ * the near field evaluated on the fly, §5.1.2).
+ *
+ * Conventions for every entry point:
+ *   - the return value is H2_OK (0) or a negative H2_E_* code; the message of
+ *     the last failure on the calling thread is h2_last_error();
+ *   - no entry point aborts the process or traps on the device;
+ *   - "host" pointers are read or written before the call returns; "device"
+ *     pointers are accessed asynchronously on the stream passed in, so the
+ *     caller keeps them alive until that stream has synchronised;
+ *   - a handle is used by one host thread / one stream at a time.
+ */
+#ifndef H2STAR_H
+#define H2STAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define H2_OK                 0
+#define H2_E_INVALID_ARG     -1   /* a size, pointer, enum or option is out of range  */
+#define H2_E_OOM             -2   /* host or device allocation failed                 */
+#define H2_E_CUDA            -3   /* a CUDA runtime call failed                       */
+#define H2_E_NOT_CONVERGED   -4   /* iterative solve stopped at maxit                 */
+#define H2_E_UNSUPPORTED     -5   /* valid request this build does not implement      */
+#define H2_E_NO_DEVICE       -6   /* no CUDA device, or the handle was built host-only */
+
+/* ---- kernel functions G(r) (diagonal value in brackets) -------------------- */
+#define H2_KERNEL_LOG2D       0   /* log r      [0]  single-layer Laplace 2D, §6.1.1   */
+#define H2_KERNEL_INVR        1   /* 1 / r      [0]  single-layer Laplace 3D, §6.2.1   */
+#define H2_KERNEL_IMQ         2   /* 1/sqrt(1+(r/c)^2) [1], c = kparam (default 0.1)   */
+#define H2_KERNEL_MATERN12    3   /* exp(-r)    [1]  Matérn nu = 1/2, App. D           */
+
+/* ---- hierarchical representations ------------------------------------------ */
+#define H2_STAR_BT            0   /* H2*(b+t),      §5.1   */
+#define H2_PLUS_H_STAR        1   /* (H2+H)*,       §5.2   */
+#define H2_SQRTD_B            2   /* H2_sqrt(d)(b), App. A */
+
+/* ---- operator storage precision ------------------------------------------- */
+#define H2_F64                0   /* operators, potentials and accumulation in fp64 */
+#define H2_F32                1   /* operators and near field in fp32, fp32 accumulate */
+
+/* Optional build settings; pass NULL for all defaults.  Zero-initialise and
+ * set the fields you need: every zero field means "default". */
+typedef struct {
+    double eps_far;        /* NCA tolerance for the far field (default: tol)           */
+    double eps_ver;        /* tolerance for vertex-sharing clusters (default: tol)     */
+    int    storage;        /* H2_F64 (default) or H2_F32                               */
+    int    kappa;          /* leaf level; 0 = smallest kappa with leaf_size 2^(d kappa) >= N
+                              (§3.1); a positive value forces that depth           */
+    int    use_domain;     /* 1: use domain_lo / domain_side as the root hyper-cube C  */
+    double domain_lo[3];   /*    lower corner of C                                    */
+    double domain_side;    /*    edge length of C; default C = tight bounding cube    */
+    int    threads;        /* host threads for the construction (default: all)        */
+    int    host_only;      /* 1: build the host representation only (no device use);
+                              h2_info / h2_get_pivots work, h2_matvec returns
+                              H2_E_NO_DEVICE                                        */
+    double kparam;         /* kernel parameter (IMQ c; default 0.1)                    */
+} h2_build_opts;
+
+typedef struct h2_handle_s* h2_handle;
+
+/*
+ * h2_build -- construct the hierarchical representation (once per geometry).
+ *
+ *   points     host, N x d row-major fp64 coordinates; copied, not retained.
+ *   N, d       N >= 1 points, d = 2 or 3.
+ *   kernel     H2_KERNEL_*.
+ *   leaf_size  n_max of §3.1 (>= 1): the tree depth kappa is the smallest with
+ *              leaf_size * 2^(d kappa) >= N unless opts->kappa forces it.
+ *   tol        ACA / NCA tolerance eps of §3.6 (> 0, < 1), used for eps_far
+ *              and eps_ver unless opts sets them (§6 uses eps = eps_far = eps_ver).
+ *   variant    H2_STAR_BT, H2_PLUS_H_STAR or H2_SQRTD_B.
+ *   opts       NULL or build options (above).
+ *   out        receives the handle (owns all host and device memory).
+ *
+ * The tree (§3.1), the interaction lists (§3.5 / §3.3), the pivots (B2T NCA
+ * Algorithm 1, T2B NCA §5.1.1, ACA §3.6) and the operators (§3.6.4) are built
+ * on the host with OpenMP; the operators are then packed per level and copied
+ * to the current CUDA device (synchronously, on the legacy default stream).
+ * Errors: H2_E_INVALID_ARG, H2_E_OOM, H2_E_CUDA, H2_E_NO_DEVICE.
+ */
+int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size,
+             double tol, int variant, const h2_build_opts* opts, h2_handle* out);
+
+/*
+ * h2_matvec -- Y = K~ X for nrhs right-hand sides (§5.1.2 / §5.2.2 / App. A.2).
+ *
+ *   X      device, fp64, column-major N x nrhs with leading dimension ldx >= N,
+ *          rows in the user's point order (the order of `points`).
+ *   Y      device, fp64, column-major N x nrhs, leading dimension ldy >= N;
+ *          overwritten.  X and Y must not overlap.
+ *   nrhs   1 <= nrhs <= 64.
+ *   stream cudaStream_t (NULL = legacy default stream); the call is asynchronous.
+ *
+ * Every step runs in this library's CUDA kernels: gather into tree order,
+ * P2M, M2M, M2L (far and vertex-sharing), L2L, L2P fused with the near field
+ * evaluated on the fly from the coordinates, scatter back.  Precision follows
+ * the build's storage (fp64, or fp32 with fp32 accumulation).
+ * Errors: H2_E_INVALID_ARG, H2_E_NO_DEVICE (host-only handle), H2_E_CUDA.
+ */
+int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
+              int nrhs, void* stream);
+
+/* Construction statistics and the per-MVP work, filled by h2_info. */
+typedef struct {
+    int64_t N;
+    int     d, kappa, kernel, variant, storage, nbases;
+    int     rank_min[2][32], rank_max[2][32];   /* [basis][level]; basis 0 far, 1 ver   */
+    double  rank_avg[2][32];
+    int64_t m2l_pairs[2];          /* stored M2L blocks per basis                          */
+    int64_t near_pairs;            /* (leaf, neighbour leaf) near-field blocks            */
+    int64_t near_evals;            /* kernel evaluations per RHS in the near field         */
+    int64_t lowrank_pairs;         /* (H2+H)*: vertex-sharing ACA blocks                   */
+    int64_t bytes_basis;           /* stored leaf bases U_X (read by P2M and L2P)          */
+    int64_t bytes_transfer;        /* stored L2L / M2M transfer matrices                   */
+    int64_t bytes_m2l;             /* stored M2L coupling matrices (rows padded to 4)      */
+    int64_t m2l_src_coeffs;        /* M2L: source coefficients gathered, summed over targets */
+    int64_t m2l_dst_coeffs;        /* M2L: target coefficients written                     */
+    int64_t vlen;                  /* multipole (= local) coefficients over all clusters   */
+    int64_t bytes_lowrank;         /* stored (H2+H)* U, V factors                          */
+    int64_t bytes_device;          /* total device bytes held by the handle                */
+    int64_t alg_bytes_per_rhs;     /* algorithmic HBM bytes of one MVP with one RHS      */
+    double  build_seconds;         /* host construction wall time                          */
+} h2_stats;
+
+/* h2_info -- fill *st (host).  Errors: H2_E_INVALID_ARG. */
+int h2_info(h2_handle h, h2_stats* st);
+
+/*
+ * h2_get_pivots -- the incoming pivots t^{X,i} (rows) and s^{X,i} (columns) of
+ * cluster `box` (bit-interleaved key) at `level` in basis `basis` (0 far /
+ * sqrt(d), 1 vertex-sharing), as user point indices in selection order.
+ * ti and si are host arrays of capacity `cap`; *rank receives the count.
+ * The outgoing pivots are t^{X,o} = s^{X,i}, s^{X,o} = t^{X,i} (symmetric
+ * kernels, same sources and targets).  Errors: H2_E_INVALID_ARG (also when
+ * cap < rank; *rank is still set).
+ */
+int h2_get_pivots(h2_handle h, int basis, int level, int64_t box, int64_t* ti,
+                  int64_t* si, int64_t cap, int* rank);
+
+/* h2_tree_order -- the permutation from tree order to user order: perm[i] is
+ * the user index of the i-th point in tree order (host array of N).  */
+int h2_tree_order(h2_handle h, int64_t* perm);
+
+/*
+ * h2_profile -- turn per-stage timing of h2_matvec on (1) or off (0) and reset
+ * the accumulated times and the launch counter.  While on, h2_matvec records
+ * CUDA events between its stages on the caller's stream (no host wait, except
+ * one read-back of the recorded events every 4096 pipeline runs).
+ * Errors: H2_E_INVALID_ARG.
+ *
+ * h2_stage_times -- accumulated milliseconds per stage since the last
+ * h2_profile call (waits for the recorded events): ms[0..7] = gather, P2M,
+ * M2M, M2L, L2L, leaf (L2P + near field), (H2+H)* low-rank, scatter;
+ * *calls = single-RHS pipeline runs timed; *launches = CUDA kernels launched
+ * by h2_matvec since the last h2_profile call (calls and launches nullable).
+ * ms is a host array with cap >= 8.  Errors: H2_E_INVALID_ARG, H2_E_CUDA.
+ */
+int h2_profile(h2_handle h, int enable);
+int h2_stage_times(h2_handle h, double* ms, int cap, int64_t* calls, int64_t* launches);
+
+/* h2_last_error -- message of the last failure on this thread ("" if none). */
+const char* h2_last_error(void);
+
+/* h2_destroy -- release the handle and all its memory (NULL is ignored).
+ * Synchronises the device first so no MVP on the handle is still running. */
+void h2_destroy(h2_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H2STAR_H */

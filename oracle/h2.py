@@ -83,8 +83,12 @@ class H2:
     """A compressed representation K~ of the kernel matrix of points P."""
 
     def __init__(self, P, kind, variant="h2star", n_max=64, eps=1e-8, eps_far=None,
-                 eps_ver=None, param=0.1, kappa=None, domain=None):
+                 eps_ver=None, param=0.1, kappa=None, domain=None, symmetric=True):
         self.P = np.asarray(P, dtype=np.float64)
+        # Remark after §3.6.4: for a symmetric kernel matrix the P2M / M2M
+        # operators are the transposes of the L2P / L2L operators.  With
+        # symmetric=False they are formed from their own formulas instead.
+        self.symmetric = symmetric
         self.kind, self.variant, self.param = kind, variant, param
         self.eps_far = eps if eps_far is None else eps_far
         self.eps_ver = eps if eps_ver is None else eps_ver
@@ -179,14 +183,15 @@ class H2:
         for X in range(t.nboxes(K)):
             tX = t.points(K, X)
             b.U[X] = _right_inv(self.K(tX, b.si[(K, X)]), lu_i[(K, X)])
-            b.Vs[X] = _left_inv(lu_o[(K, X)], self.K(b.to[(K, X)], tX))
+            b.Vs[X] = b.U[X].T if self.symmetric else \
+                _left_inv(lu_o[(K, X)], self.K(b.to[(K, X)], tX))
         for l in range(b.lmin, K):
             for X in range(t.nboxes(l)):
                 for c in t.children(X):
                     b.Ut[(l + 1, c)] = _right_inv(self.K(b.ti[(l + 1, c)], b.si[(l, X)]),
                                                   lu_i[(l, X)])
-                    b.Vt[(l + 1, c)] = _left_inv(lu_o[(l, X)],
-                                                 self.K(b.to[(l, X)], b.so[(l + 1, c)]))
+                    b.Vt[(l + 1, c)] = b.Ut[(l + 1, c)].T if self.symmetric else \
+                        _left_inv(lu_o[(l, X)], self.K(b.to[(l, X)], b.so[(l + 1, c)]))
         for l in range(b.lmin, K + 1):
             for X in range(t.nboxes(l)):
                 for Y in b.il[(l, X)]:

@@ -1,0 +1,204 @@
+"""GB300 (sm_103a) H2* fast matrix-vector product -- Python binding.
+
+Thin ctypes binding over the C ABI declared in ``include/h2star.h``.  It only
+marshals arguments: the hierarchical construction runs in the library's C++
+host code, and every step of the matrix-vector product runs in its CUDA
+kernels.  PyTorch is used for device memory and streams only.  There is no
+CPU fallback: if ``libh2star.so`` is missing, every call raises.
+
+    from paper_2309_14085_gb300 import H2Matrix
+    A = H2Matrix(points, "log2d", leaf_size=64, tol=1e-8)       # host build + upload
+    y = A.matvec(x)        # x: torch float64 CUDA tensor (N,) or (N, nrhs)
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libh2star.so")
+
+KERNELS = {"log2d": 0, "invr": 1, "imq": 2, "matern12": 3}
+VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2}
+STORAGE = {"f64": 0, "f32": 1}
+STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
+EXPORTED = ("h2_build", "h2_matvec", "h2_info", "h2_get_pivots", "h2_tree_order",
+            "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy")
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("eps_far", ctypes.c_double), ("eps_ver", ctypes.c_double),
+                ("storage", ctypes.c_int), ("kappa", ctypes.c_int),
+                ("use_domain", ctypes.c_int), ("domain_lo", ctypes.c_double * 3),
+                ("domain_side", ctypes.c_double), ("threads", ctypes.c_int),
+                ("host_only", ctypes.c_int), ("kparam", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("d", ctypes.c_int), ("kappa", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("variant", ctypes.c_int), ("storage", ctypes.c_int),
+                ("nbases", ctypes.c_int),
+                ("rank_min", (ctypes.c_int * 32) * 2), ("rank_max", (ctypes.c_int * 32) * 2),
+                ("rank_avg", (ctypes.c_double * 32) * 2),
+                ("m2l_pairs", ctypes.c_int64 * 2), ("near_pairs", ctypes.c_int64),
+                ("near_evals", ctypes.c_int64), ("lowrank_pairs", ctypes.c_int64),
+                ("bytes_basis", ctypes.c_int64), ("bytes_transfer", ctypes.c_int64),
+                ("bytes_m2l", ctypes.c_int64), ("m2l_src_coeffs", ctypes.c_int64),
+                ("m2l_dst_coeffs", ctypes.c_int64), ("vlen", ctypes.c_int64),
+                ("bytes_lowrank", ctypes.c_int64),
+                ("bytes_device", ctypes.c_int64), ("alg_bytes_per_rhs", ctypes.c_int64),
+                ("build_seconds", ctypes.c_double)]
+
+
+class H2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"h2 error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libh2star.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2309_14085_gb300.build_lib`")
+        L = ctypes.CDLL(LIB_PATH)
+        c_i64, c_int, c_vp, c_dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+        L.h2_build.argtypes = [c_vp, c_i64, c_int, c_int, c_int, c_dbl, c_int,
+                               ctypes.POINTER(BuildOpts), ctypes.POINTER(c_vp)]
+        L.h2_matvec.argtypes = [c_vp, c_vp, c_i64, c_vp, c_i64, c_int, c_vp]
+        L.h2_info.argtypes = [c_vp, ctypes.POINTER(Stats)]
+        L.h2_get_pivots.argtypes = [c_vp, c_int, c_int, c_i64, c_vp, c_vp, c_i64,
+                                    ctypes.POINTER(c_int)]
+        L.h2_tree_order.argtypes = [c_vp, c_vp]
+        L.h2_profile.argtypes = [c_vp, c_int]
+        L.h2_stage_times.argtypes = [c_vp, c_vp, c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]
+        L.h2_last_error.restype = ctypes.c_char_p
+        L.h2_destroy.argtypes = [c_vp]
+        L.h2_destroy.restype = None
+        for name in EXPORTED:
+            if name not in ("h2_last_error", "h2_destroy"):
+                getattr(L, name).restype = c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise H2Error(rc, lib().h2_last_error().decode())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class H2Matrix:
+    """A compressed kernel matrix K~ (H2*(b+t), (H2+H)* or H2_sqrt(d)(b))."""
+
+    def __init__(self, points, kernel, leaf_size=64, tol=1e-8, variant="h2star", storage="f64",
+                 eps_far=None, eps_ver=None, kappa=None, domain=None, threads=0,
+                 host_only=False, kparam=None):
+        P = np.ascontiguousarray(points, dtype=np.float64)
+        if P.ndim != 2:
+            raise ValueError("points must be N x d")
+        self.N, self.d = P.shape
+        self.kernel, self.variant, self.storage = kernel, variant, storage
+        o = BuildOpts()
+        o.eps_far = eps_far or 0.0
+        o.eps_ver = eps_ver or 0.0
+        o.storage = STORAGE[storage]
+        o.kappa = kappa or 0
+        if domain is not None:
+            lo, side = domain
+            o.use_domain = 1
+            for k in range(self.d):
+                o.domain_lo[k] = float(lo[k])
+            o.domain_side = float(side)
+        o.threads = threads
+        o.host_only = int(host_only)
+        o.kparam = kparam or 0.0
+        h = ctypes.c_void_p()
+        _check(lib().h2_build(P.ctypes.data, self.N, self.d, KERNELS[kernel], leaf_size, tol,
+                              VARIANTS[variant], ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    # -- the product ---------------------------------------------------------
+    def matvec(self, X, out=None, stream=None):
+        """Y = K~ X for a float64 CUDA tensor X of shape (N,) or (N, nrhs)."""
+        import torch
+        if X.dtype != torch.float64 or not X.is_cuda:
+            raise ValueError("X must be a float64 CUDA tensor")
+        vec = X.dim() == 1
+        X2 = X.reshape(self.N, 1) if vec else X
+        nrhs = X2.shape[1]
+        Xc = X2 if (X2.stride(0) == 1 and (nrhs == 1 or X2.stride(1) >= self.N)) else \
+            X2.t().contiguous().t()
+        ldx = self.N if nrhs == 1 else Xc.stride(1)
+        if out is None:
+            Y = torch.empty((nrhs, self.N), dtype=torch.float64, device=X.device).t()
+        else:
+            Y = out.reshape(self.N, 1) if out.dim() == 1 else out
+            if Y.stride(0) != 1:
+                raise ValueError("out must be column-major")
+        ldy = self.N if nrhs == 1 else Y.stride(1)
+        _check(lib().h2_matvec(self._h, ctypes.c_void_p(Xc.data_ptr()), ldx,
+                               ctypes.c_void_p(Y.data_ptr()), ldy, nrhs, _stream_ptr(stream)))
+        if out is not None:
+            return out
+        return Y.reshape(self.N) if vec else Y
+
+    # -- introspection -----------------------------------------------------------
+    def info(self):
+        st = Stats()
+        _check(lib().h2_info(self._h, ctypes.byref(st)))
+        out = {f[0]: getattr(st, f[0]) for f in Stats._fields_
+               if f[0] not in ("rank_min", "rank_max", "rank_avg", "m2l_pairs")}
+        out["m2l_pairs"] = list(st.m2l_pairs)
+        out["ranks"] = [{l: (st.rank_min[b][l], round(st.rank_avg[b][l], 2), st.rank_max[b][l])
+                         for l in range(st.kappa + 1) if st.rank_max[b][l] > 0}
+                        for b in range(st.nbases)]
+        return out
+
+    def pivots(self, basis, level, box):
+        """(t^{X,i}, s^{X,i}) as user point indices, in selection order."""
+        cap = 4096
+        ti = np.zeros(cap, dtype=np.int64)
+        si = np.zeros(cap, dtype=np.int64)
+        r = ctypes.c_int()
+        _check(lib().h2_get_pivots(self._h, basis, level, box, ti.ctypes.data, si.ctypes.data,
+                                   cap, ctypes.byref(r)))
+        return ti[:r.value].copy(), si[:r.value].copy()
+
+    def tree_order(self):
+        perm = np.zeros(self.N, dtype=np.int64)
+        _check(lib().h2_tree_order(self._h, perm.ctypes.data))
+        return perm
+
+    def profile(self, enable=True):
+        _check(lib().h2_profile(self._h, int(enable)))
+
+    def stage_times(self):
+        """(ms per stage accumulated, pipeline runs timed, kernels launched)."""
+        ms = np.zeros(8)
+        calls, launches = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().h2_stage_times(self._h, ms.ctypes.data, 8, ctypes.byref(calls),
+                                    ctypes.byref(launches)))
+        return dict(zip(STAGES, ms.tolist())), calls.value, launches.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().h2_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,757 @@
+// Host construction of H2*(b+t), (H2+H)* and H2_sqrt(d)(b):
+//   tree (§3.1), lists (§3.5 / §3.3), partially pivoted ACA (§3.6),
+//   B2T NCA (Algorithm 1), T2B NCA (§5.1.1 item 2), pure ACA of the
+//   vertex-sharing blocks (Algorithm 3), operators (§3.6.4) and the packed
+//   level-batched layout the CUDA kernels read.
+//
+// Compiled with -ffp-contract=off so that the arithmetic is the same on x86
+// and Arm hosts (no fused multiply-add contraction).
+#include <omp.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+
+#include "h2_internal.hpp"
+
+namespace h2 {
+namespace {
+
+int64_t morton(const int* c, int level, int d) {
+    int64_t key = 0;
+    for (int b = 0; b < level; ++b)
+        for (int k = 0; k < d; ++k) key |= int64_t((c[k] >> b) & 1) << (b * d + k);
+    return key;
+}
+
+void demorton(int64_t key, int level, int d, int* c) {
+    for (int k = 0; k < d; ++k) c[k] = 0;
+    for (int b = 0; b < level; ++b)
+        for (int k = 0; k < d; ++k) c[k] |= int((key >> (b * d + k)) & 1) << b;
+}
+
+// 'self' 0, far 1, vertex-sharing 2, other neighbour (shares a d'-surface, d' >= 1) 3
+int classify(const int* a, const int* b, int d) {
+    int m = 0, neq = 0;
+    for (int k = 0; k < d; ++k) {
+        const int t = std::abs(a[k] - b[k]);
+        m = std::max(m, t);
+        neq += (t == 0);
+    }
+    if (m == 0) return 0;
+    if (m >= 2) return 1;
+    return neq == 0 ? 2 : 3;
+}
+
+// ---------------------------------------------------------------------------
+// Tree (§3.1)
+void build_tree(Tree& t, const double* P, int64_t N, int d, int leaf_size, int kappa_forced,
+                const double* dom_lo, double dom_side) {
+    t.N = N;
+    t.d = d;
+    if (kappa_forced > 0) {
+        t.kappa = kappa_forced;
+    } else {
+        int k = 0;
+        while (double(leaf_size) * double(int64_t(1) << (d * k)) < double(N)) ++k;
+        t.kappa = k;
+    }
+    if (dom_lo) {
+        for (int k = 0; k < d; ++k) t.lo[k] = dom_lo[k];
+        t.side = dom_side;
+    } else {
+        double hi[3];
+        for (int k = 0; k < d; ++k) { t.lo[k] = P[k]; hi[k] = P[k]; }
+        for (int64_t i = 1; i < N; ++i)
+            for (int k = 0; k < d; ++k) {
+                t.lo[k] = std::min(t.lo[k], P[i * d + k]);
+                hi[k] = std::max(hi[k], P[i * d + k]);
+            }
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s = std::max(s, hi[k] - t.lo[k]);
+        t.side = s > 0.0 ? s : 1.0;
+    }
+    const double scale = double(int64_t(1) << t.kappa);
+    const int cmax = (1 << t.kappa) - 1;
+    std::vector<int64_t> key(N);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        int c[3];
+        for (int k = 0; k < d; ++k) {
+            const double f = std::floor((P[i * d + k] - t.lo[k]) / t.side * scale);
+            int ci = f < 0.0 ? 0 : (f > double(cmax) ? cmax : int(f));
+            c[k] = ci;
+        }
+        key[i] = morton(c, t.kappa, d);
+    }
+    t.perm.resize(N);
+    std::iota(t.perm.begin(), t.perm.end(), int64_t(0));
+    std::stable_sort(t.perm.begin(), t.perm.end(),
+                     [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+    const int64_t nleaf = t.nboxes(t.kappa);
+    t.leaf_ptr.assign(nleaf + 1, 0);
+    for (int64_t i = 0; i < N; ++i) t.leaf_ptr[key[i] + 1]++;
+    for (int64_t L = 0; L < nleaf; ++L) t.leaf_ptr[L + 1] += t.leaf_ptr[L];
+    t.x.resize(size_t(N) * d);
+    for (int64_t i = 0; i < N; ++i)
+        for (int k = 0; k < d; ++k) t.x[i * d + k] = P[t.perm[i] * d + k];
+}
+
+// ---------------------------------------------------------------------------
+// Lists (§3.5 weak admissibility with IL_far / IL_ver, §3.3 strong with eta = sqrt d)
+void build_lists(const Tree& t, Lists& L) {
+    const int d = t.d, K = t.kappa;
+    L.far.assign(K + 1, Csr());
+    L.ver.assign(K + 1, Csr());
+    L.sqrtd.assign(K + 1, Csr());
+    for (int l = 0; l <= K; ++l) {
+        const int64_t n = t.nboxes(l);
+        const int side = 1 << l;
+        std::vector<std::vector<int64_t>> F(n), V(n), S(n);
+        if (l >= 1) {
+#pragma omp parallel for schedule(static)
+            for (int64_t X = 0; X < n; ++X) {
+                int c[3], p[3];
+                demorton(X, l, d, c);
+                for (int k = 0; k < d; ++k) p[k] = c[k] >> 1;
+                const int nofs = (d == 2) ? 9 : 27;
+                for (int o = 0; o < nofs; ++o) {
+                    int q[3], nzero = 0;
+                    bool ok = true;
+                    int oo = o;
+                    for (int k = 0; k < d; ++k) {
+                        const int off = oo % 3 - 1;
+                        oo /= 3;
+                        q[k] = p[k] + off;
+                        nzero += (off == 0);
+                        if (q[k] < 0 || q[k] >= (side >> 1)) ok = false;
+                    }
+                    if (!ok) continue;
+                    // parent neighbour in N_* (self or sharing a d'-surface, d' >= 1)
+                    const bool in_near_star = nzero >= 1;
+                    for (int ch = 0; ch < (1 << d); ++ch) {
+                        int cc[3];
+                        for (int k = 0; k < d; ++k) cc[k] = 2 * q[k] + ((ch >> k) & 1);
+                        const int cls = classify(c, cc, d);
+                        const int64_t key = morton(cc, l, d);
+                        if (cls == 1) S[X].push_back(key);       // IL_sqrt: far, parent in N_sqrt
+                        if (!in_near_star || cls == 0) continue;
+                        if (cls == 1) F[X].push_back(key);
+                        else if (cls == 2) V[X].push_back(key);
+                    }
+                }
+                std::sort(F[X].begin(), F[X].end());
+                std::sort(V[X].begin(), V[X].end());
+                std::sort(S[X].begin(), S[X].end());
+            }
+        }
+        auto pack = [n](std::vector<std::vector<int64_t>>& src, Csr& dst) {
+            dst.ptr.assign(n + 1, 0);
+            for (int64_t X = 0; X < n; ++X) dst.ptr[X + 1] = dst.ptr[X] + int64_t(src[X].size());
+            dst.idx.resize(dst.ptr[n]);
+            for (int64_t X = 0; X < n; ++X)
+                std::copy(src[X].begin(), src[X].end(), dst.idx.begin() + dst.ptr[X]);
+        };
+        pack(F, L.far[l]);
+        pack(V, L.ver[l]);
+        pack(S, L.sqrtd[l]);
+    }
+    // leaf near fields
+    const int64_t n = t.nboxes(K);
+    const int side = 1 << K;
+    std::vector<std::vector<int64_t>> NS(n), NQ(n);
+#pragma omp parallel for schedule(static)
+    for (int64_t X = 0; X < n; ++X) {
+        int c[3];
+        demorton(X, K, d, c);
+        const int nofs = (d == 2) ? 9 : 27;
+        for (int o = 0; o < nofs; ++o) {
+            int q[3];
+            bool ok = true;
+            int oo = o;
+            for (int k = 0; k < d; ++k) {
+                q[k] = c[k] + oo % 3 - 1;
+                oo /= 3;
+                if (q[k] < 0 || q[k] >= side) ok = false;
+            }
+            if (!ok) continue;
+            const int cls = classify(c, q, d);
+            const int64_t key = morton(q, K, d);
+            NQ[X].push_back(key);
+            if (cls == 0 || cls == 3) NS[X].push_back(key);
+        }
+        std::sort(NS[X].begin(), NS[X].end());
+        std::sort(NQ[X].begin(), NQ[X].end());
+    }
+    auto pack = [n](std::vector<std::vector<int64_t>>& src, Csr& dst) {
+        dst.ptr.assign(n + 1, 0);
+        for (int64_t X = 0; X < n; ++X) dst.ptr[X + 1] = dst.ptr[X] + int64_t(src[X].size());
+        dst.idx.resize(dst.ptr[n]);
+        for (int64_t X = 0; X < n; ++X)
+            std::copy(src[X].begin(), src[X].end(), dst.idx.begin() + dst.ptr[X]);
+    };
+    pack(NS, L.near_star);
+    pack(NQ, L.near_sqrt);
+}
+
+// ---------------------------------------------------------------------------
+// Partially pivoted ACA (§3.6), in the reading documented with the oracle:
+// first row first; residual row; column pivot = first argmax over unused
+// columns; zero row -> next unused row; residual column; incremental
+// Frobenius norm; stop after accepting a pivot with |u||v| <= eps ||S||_F;
+// next row = first argmax of |u| over unused rows.
+struct AcaResult {
+    std::vector<int> rows, cols;
+    std::vector<std::vector<double>> us, vs;   // kept only when requested
+};
+
+void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
+         const std::vector<int64_t>& J, double eps, bool keep, AcaResult& out) {
+    out.rows.clear();
+    out.cols.clear();
+    out.us.clear();
+    out.vs.clear();
+    const int64_t nI = int64_t(I.size()), nJ = int64_t(J.size());
+    if (nI == 0 || nJ == 0) return;
+    const int d = t.d;
+    std::vector<double> xI(nI * d), xJ(nJ * d);
+    for (int64_t i = 0; i < nI; ++i)
+        for (int k = 0; k < d; ++k) xI[i * d + k] = t.x[I[i] * d + k];
+    for (int64_t j = 0; j < nJ; ++j)
+        for (int k = 0; k < d; ++k) xJ[j * d + k] = t.x[J[j] * d + k];
+    auto entry = [&](int64_t i, int64_t j) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) { const double q = xI[i * d + k] - xJ[j * d + k]; s = s + q * q; }
+        return G(s);
+    };
+    std::vector<std::vector<double>>& us = out.us;
+    std::vector<std::vector<double>>& vs = out.vs;
+    std::vector<char> row_used(nI, 0), col_used(nJ, 0);
+    std::vector<double> r(nJ), u(nI);
+    double S2 = 0.0;
+    int64_t i = 0;
+    const int64_t kmax = std::min(nI, nJ);
+    auto next_free_row = [&]() -> int64_t {
+        for (int64_t a = 0; a < nI; ++a)
+            if (!row_used[a]) return a;
+        return -1;
+    };
+    while (int64_t(out.rows.size()) < kmax) {
+        for (int64_t j = 0; j < nJ; ++j) r[j] = entry(i, j);
+        for (size_t l = 0; l < us.size(); ++l) {
+            const double a = us[l][i];
+            const double* vl = vs[l].data();
+            for (int64_t j = 0; j < nJ; ++j) r[j] = r[j] - a * vl[j];
+        }
+        row_used[i] = 1;
+        int64_t jb = -1;
+        double best = -1.0;
+        for (int64_t j = 0; j < nJ; ++j) {
+            const double a = col_used[j] ? -1.0 : std::fabs(r[j]);
+            if (a > best) { best = a; jb = j; }
+        }
+        if (best <= 0.0) {
+            i = next_free_row();
+            if (i < 0) break;
+            continue;
+        }
+        const double piv = r[jb];
+        std::vector<double> v(nJ);
+        for (int64_t j = 0; j < nJ; ++j) v[j] = r[j] / piv;
+        for (int64_t a = 0; a < nI; ++a) u[a] = entry(a, jb);
+        for (size_t l = 0; l < us.size(); ++l) {
+            const double b = vs[l][jb];
+            const double* ul = us[l].data();
+            for (int64_t a = 0; a < nI; ++a) u[a] = u[a] - b * ul[a];
+        }
+        col_used[jb] = 1;
+        double uu = 0.0, vv = 0.0, cross = 0.0;
+        for (int64_t a = 0; a < nI; ++a) uu += u[a] * u[a];
+        for (int64_t j = 0; j < nJ; ++j) vv += v[j] * v[j];
+        for (size_t l = 0; l < us.size(); ++l) {
+            double pu = 0.0, pv = 0.0;
+            for (int64_t a = 0; a < nI; ++a) pu += us[l][a] * u[a];
+            for (int64_t j = 0; j < nJ; ++j) pv += vs[l][j] * v[j];
+            cross += pu * pv;
+        }
+        S2 = S2 + 2.0 * cross + uu * vv;
+        us.emplace_back(u);
+        vs.emplace_back(std::move(v));
+        out.rows.push_back(int(i));
+        out.cols.push_back(int(jb));
+        if (std::sqrt(uu) * std::sqrt(vv) <= eps * std::sqrt(std::max(S2, 0.0))) break;
+        int64_t ib = -1;
+        best = -1.0;
+        for (int64_t a = 0; a < nI; ++a) {
+            const double q = row_used[a] ? -1.0 : std::fabs(u[a]);
+            if (q > best) { best = q; ib = a; }
+        }
+        if (best <= 0.0) {
+            i = next_free_row();
+            if (i < 0) break;
+        } else {
+            i = ib;
+        }
+    }
+    if (!keep) {
+        us.clear();
+        vs.clear();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dense LU with partial pivoting (row-major n x n, in place) and solves.
+bool lu_factor(std::vector<double>& A, int n, std::vector<int>& piv) {
+    piv.resize(n);
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        double best = std::fabs(A[size_t(k) * n + k]);
+        for (int i = k + 1; i < n; ++i) {
+            const double a = std::fabs(A[size_t(i) * n + k]);
+            if (a > best) { best = a; p = i; }
+        }
+        piv[k] = p;
+        if (best == 0.0) return false;
+        if (p != k)
+            for (int j = 0; j < n; ++j) std::swap(A[size_t(k) * n + j], A[size_t(p) * n + j]);
+        const double inv = A[size_t(k) * n + k];
+        for (int i = k + 1; i < n; ++i) {
+            const double f = A[size_t(i) * n + k] / inv;
+            A[size_t(i) * n + k] = f;
+            if (f != 0.0)
+                for (int j = k + 1; j < n; ++j)
+                    A[size_t(i) * n + j] = A[size_t(i) * n + j] - f * A[size_t(k) * n + j];
+        }
+    }
+    return true;
+}
+
+void lu_solve(const std::vector<double>& A, int n, const std::vector<int>& piv, double* b) {
+    for (int k = 0; k < n; ++k) std::swap(b[k], b[piv[k]]);
+    for (int i = 1; i < n; ++i) {
+        double s = b[i];
+        for (int j = 0; j < i; ++j) s = s - A[size_t(i) * n + j] * b[j];
+        b[i] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int j = i + 1; j < n; ++j) s = s - A[size_t(i) * n + j] * b[j];
+        b[i] = s / A[size_t(i) * n + i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pivot selection
+void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps) {
+    const Tree& t = H.tree;
+    const int K = t.kappa, d = t.d;
+    B.lmin = 2;
+    B.il = &il;
+    B.tau.assign(K + 1, {});
+    B.sig.assign(K + 1, {});
+    for (int l = 0; l <= K; ++l) { B.tau[l].resize(t.nboxes(l)); B.sig[l].resize(t.nboxes(l)); }
+    for (int l = K; l >= 2; --l) {
+        const int64_t n = t.nboxes(l);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t X = 0; X < n; ++X) {
+            std::vector<int64_t> I, J;
+            const Csr& L = il[l];
+            if (l == K) {
+                for (int64_t p = t.begin(l, X); p < t.end(l, X); ++p) I.push_back(p);
+                for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
+                    const int64_t Y = L.idx[e];
+                    for (int64_t p = t.begin(l, Y); p < t.end(l, Y); ++p) J.push_back(p);
+                }
+            } else {
+                for (int c = 0; c < (1 << d); ++c) {
+                    const auto& tc = B.tau[l + 1][X * (int64_t(1) << d) + c];
+                    I.insert(I.end(), tc.begin(), tc.end());
+                }
+                for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
+                    const int64_t Y = L.idx[e];
+                    for (int c = 0; c < (1 << d); ++c) {   // s^{Y_c,o} = t^{Y_c,i}
+                        const auto& tc = B.tau[l + 1][Y * (int64_t(1) << d) + c];
+                        J.insert(J.end(), tc.begin(), tc.end());
+                    }
+                }
+            }
+            AcaResult R;
+            aca(t, H.kern, I, J, eps, false, R);
+            auto& tau = B.tau[l][X];
+            auto& sig = B.sig[l][X];
+            for (int a : R.rows) tau.push_back(I[a]);
+            for (int a : R.cols) sig.push_back(J[a]);
+        }
+    }
+}
+
+void t2b(const Host& H, Basis& B, const std::vector<Csr>& il, double eps) {
+    const Tree& t = H.tree;
+    const int K = t.kappa, d = t.d;
+    B.lmin = 1;
+    B.il = &il;
+    B.tau.assign(K + 1, {});
+    B.sig.assign(K + 1, {});
+    for (int l = 0; l <= K; ++l) { B.tau[l].resize(t.nboxes(l)); B.sig[l].resize(t.nboxes(l)); }
+    for (int l = 1; l <= K; ++l) {
+        const int64_t n = t.nboxes(l);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t X = 0; X < n; ++X) {
+            std::vector<int64_t> I, J;
+            const Csr& L = il[l];
+            for (int64_t p = t.begin(l, X); p < t.end(l, X); ++p) I.push_back(p);
+            for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
+                const int64_t Y = L.idx[e];
+                for (int64_t p = t.begin(l, Y); p < t.end(l, Y); ++p) J.push_back(p);
+            }
+            if (l > 1) {
+                const auto& sp = B.sig[l - 1][X >> d];
+                J.insert(J.end(), sp.begin(), sp.end());
+            }
+            AcaResult R;
+            aca(t, H.kern, I, J, eps, false, R);
+            for (int a : R.rows) B.tau[l][X].push_back(I[a]);
+            for (int a : R.cols) B.sig[l][X].push_back(J[a]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Operators (§3.6.4), symmetric reading: U_X = K_{t^X,s^{X,i}} (K_{t^{X,i},s^{X,i}})^{-1},
+// L2L U~_{X_c X} = K_{t^{X_c,i}, s^{X,i}} (K_{t^{X,i},s^{X,i}})^{-1}, P2M / M2M their
+// transposes, M2L T_{X,Y} = K_{t^{X,i}, t^{Y,i}}.
+std::string operators(const Host& H, Basis& B) {
+    const Tree& t = H.tree;
+    const int K = t.kappa, d = t.d;
+    B.U.assign(t.nboxes(K), {});
+    B.Ut.assign(K + 1, {});
+    B.T.assign(K + 1, {});
+    if (K < B.lmin) return "";
+    for (int l = 0; l <= K; ++l) { B.Ut[l].resize(t.nboxes(l)); B.T[l].resize(t.nboxes(l)); }
+    std::string err;
+    for (int l = B.lmin; l <= K; ++l) {
+        const int64_t n = t.nboxes(l);
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t X = 0; X < n; ++X) {
+            const auto& tau = B.tau[l][X];
+            const auto& sig = B.sig[l][X];
+            const int r = int(tau.size());
+            // Pt = (K_{tau, sig})^T, factorised once; rows of B A^{-1} solve Pt x = b
+            std::vector<double> Pt(size_t(r) * r);
+            std::vector<int> piv;
+            for (int a = 0; a < r; ++a)
+                for (int b = 0; b < r; ++b) Pt[size_t(a) * r + b] = H.kern(t.r2(tau[b], sig[a]));
+            if (r > 0 && !lu_factor(Pt, r, piv)) {
+#pragma omp critical
+                err = "singular pivot matrix";
+                continue;
+            }
+            auto solve_rows = [&](const std::vector<int64_t>& rows, std::vector<double>& out) {
+                out.resize(rows.size() * size_t(r));
+                for (size_t i = 0; i < rows.size(); ++i) {
+                    double* b = out.data() + i * r;
+                    for (int a = 0; a < r; ++a) b[a] = H.kern(t.r2(rows[i], sig[a]));
+                    lu_solve(Pt, r, piv, b);
+                }
+            };
+            if (l == K) {
+                std::vector<int64_t> pts;
+                for (int64_t p = t.begin(l, X); p < t.end(l, X); ++p) pts.push_back(p);
+                solve_rows(pts, B.U[X]);
+            }
+            if (l < K)
+                for (int c = 0; c < (1 << d); ++c) {
+                    const int64_t Xc = X * (int64_t(1) << d) + c;
+                    solve_rows(B.tau[l + 1][Xc], B.Ut[l + 1][Xc]);
+                }
+            // M2L: concatenated T_{X,Y} over Y in the list, r_X x sum r_Y
+            const Csr& L = (*B.il)[l];
+            int64_t kx = 0;
+            for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) kx += B.rank(l, L.idx[e]);
+            auto& T = B.T[l][X];
+            T.assign(size_t(r) * kx, 0.0);
+            int64_t col = 0;
+            for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
+                const auto& ty = B.tau[l][L.idx[e]];
+                for (int a = 0; a < r; ++a)
+                    for (size_t b = 0; b < ty.size(); ++b)
+                        T[size_t(a) * kx + col + b] = H.kern(t.r2(tau[a], ty[b]));
+                col += int64_t(ty.size());
+            }
+        }
+    }
+    return err;
+}
+
+void pure_aca(Host& H) {
+    const Tree& t = H.tree;
+    const int K = t.kappa;
+    std::vector<std::pair<int, std::pair<int64_t, int64_t>>> pairs;
+    for (int l = 1; l <= K; ++l)
+        for (int64_t X = 0; X < t.nboxes(l); ++X)
+            for (int64_t e = H.lists.ver[l].ptr[X]; e < H.lists.ver[l].ptr[X + 1]; ++e)
+                pairs.push_back({l, {X, H.lists.ver[l].idx[e]}});
+    H.lowrank.assign(pairs.size(), LowRankBlock());
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t p = 0; p < int64_t(pairs.size()); ++p) {
+        const int l = pairs[p].first;
+        const int64_t X = pairs[p].second.first, Y = pairs[p].second.second;
+        std::vector<int64_t> I, J;
+        for (int64_t a = t.begin(l, X); a < t.end(l, X); ++a) I.push_back(a);
+        for (int64_t a = t.begin(l, Y); a < t.end(l, Y); ++a) J.push_back(a);
+        AcaResult R;
+        aca(t, H.kern, I, J, H.eps_ver, true, R);
+        LowRankBlock& B = H.lowrank[p];
+        B.level = l;
+        B.X = X;
+        B.Y = Y;
+        B.k = int(R.rows.size());
+        B.U.resize(I.size() * size_t(B.k));
+        B.V.resize(J.size() * size_t(B.k));
+        for (int k = 0; k < B.k; ++k) {
+            std::copy(R.us[k].begin(), R.us[k].end(), B.U.begin() + size_t(k) * I.size());
+            std::copy(R.vs[k].begin(), R.vs[k].end(), B.V.begin() + size_t(k) * J.size());
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packing into the flat level-batched layout read by the kernels.
+void pack(Host& H) {
+    const Tree& t = H.tree;
+    const int K = t.kappa, d = t.d;
+    Packed& P = H.packed;
+    P.nb = int(H.bases.size());
+    P.box_base.assign(K + 2, 0);
+    for (int l = 0; l <= K; ++l) P.box_base[l + 1] = P.box_base[l] + t.nboxes(l);
+    P.box_total = P.box_base[K + 1];
+    const int64_t ns = P.nb * P.box_total;
+    P.rank.assign(ns, 0);
+    P.voff.assign(ns, 0);
+    P.uoff.assign(ns, -1);
+    P.utoff.assign(ns, -1);
+    auto slot = [&](int b, int l, int64_t X) { return b * P.box_total + P.box_base[l] + X; };
+    int64_t vo = 0;
+    for (int b = 0; b < P.nb; ++b)
+        for (int l = 0; l <= K; ++l)
+            for (int64_t X = 0; X < t.nboxes(l); ++X) {
+                const int64_t s = slot(b, l, X);
+                const int r = (l >= H.bases[b].lmin && l <= K) ? H.bases[b].rank(l, X) : 0;
+                P.rank[s] = r;
+                P.voff[s] = vo;
+                vo += r;
+            }
+    P.vlen = vo;
+    // ---- first pass: the offset of every block (each block starts on a
+    //      multiple of 4 elements), then one allocation and a parallel copy
+    int64_t total = 0;
+    auto place = [&](int64_t n) {
+        const int64_t o = (total + 3) / 4 * 4;
+        total = o + n;
+        return o;
+    };
+    struct Copy { const std::vector<double>* src; int64_t dst; int64_t rows, cols, pad; };
+    std::vector<Copy> copies;
+    for (int b = 0; b < P.nb; ++b) {
+        const Basis& B = H.bases[b];
+        if (K < B.lmin) continue;
+        for (int64_t X = 0; X < t.nboxes(K); ++X) {
+            const int64_t o = place(int64_t(B.U[X].size()));
+            P.uoff[slot(b, K, X)] = o;
+            copies.push_back({&B.U[X], o, 1, int64_t(B.U[X].size()), int64_t(B.U[X].size())});
+        }
+    }
+    for (int b = 0; b < P.nb; ++b) {
+        const Basis& B = H.bases[b];
+        for (int l = B.lmin + 1; l <= K; ++l)
+            for (int64_t X = 0; X < t.nboxes(l); ++X) {
+                const int64_t o = place(int64_t(B.Ut[l][X].size()));
+                P.utoff[slot(b, l, X)] = o;
+                copies.push_back({&B.Ut[l][X], o, 1, int64_t(B.Ut[l][X].size()),
+                                  int64_t(B.Ut[l][X].size())});
+            }
+    }
+    P.m2m_tasks.assign(K + 1, {});
+    P.l2l_tasks.assign(K + 1, {});
+    for (int b = 0; b < P.nb; ++b) {
+        const Basis& B = H.bases[b];
+        for (int l = B.lmin; l < K; ++l)
+            for (int64_t X = 0; X < t.nboxes(l); ++X)
+                if (B.rank(l, X) > 0) P.m2m_tasks[l].push_back(slot(b, l, X));
+        for (int l = B.lmin + 1; l <= K; ++l)
+            for (int64_t X = 0; X < t.nboxes(l); ++X)
+                if (B.rank(l, X) > 0 && B.rank(l - 1, X >> d) > 0)
+                    P.l2l_tasks[l].push_back(slot(b, l, X));
+    }
+    // M2L: rows padded with zeros to a multiple of 4 columns
+    P.m2l_slot.clear();
+    P.m2l_toff.clear();
+    P.m2l_k.clear();
+    P.m2l_kpad.clear();
+    P.m2l_src_ptr.assign(1, 0);
+    P.m2l_src.clear();
+    P.m2l_kpad_max = 0;
+    P.m2l_entries = 0;
+    for (int b = 0; b < P.nb; ++b) {
+        const Basis& B = H.bases[b];
+        for (int l = B.lmin; l <= K; ++l) {
+            const Csr& L = (*B.il)[l];
+            for (int64_t X = 0; X < t.nboxes(l); ++X) {
+                const int r = B.rank(l, X);
+                int64_t kx = 0;
+                for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) kx += B.rank(l, L.idx[e]);
+                if (r == 0 || kx == 0) continue;
+                const int64_t kp = (kx + 3) / 4 * 4;
+                const int64_t o = place(int64_t(r) * kp);
+                P.m2l_slot.push_back(slot(b, l, X));
+                P.m2l_toff.push_back(o);
+                P.m2l_k.push_back(int32_t(kx));
+                P.m2l_kpad.push_back(int32_t(kp));
+                P.m2l_kpad_max = std::max<int32_t>(P.m2l_kpad_max, int32_t(kp));
+                P.m2l_entries += int64_t(r) * kp;
+                copies.push_back({&B.T[l][X], o, r, kx, kp});
+                for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
+                    const int64_t Y = L.idx[e];
+                    if (B.rank(l, Y) > 0) P.m2l_src.push_back(slot(b, l, Y));
+                }
+                P.m2l_src_ptr.push_back(int64_t(P.m2l_src.size()));
+            }
+        }
+    }
+    const Csr& NL = (H.variant == 2) ? H.lists.near_sqrt : H.lists.near_star;
+    P.near_ptr = NL.ptr;
+    P.near_idx = NL.idx;
+    // (H2+H)* factors grouped by level (blocks of one target stay consecutive)
+    P.lr_level_ptr.assign(K + 2, 0);
+    P.lr_x0.clear(); P.lr_mx.clear(); P.lr_y0.clear(); P.lr_my.clear();
+    P.lr_uoff.clear(); P.lr_voff.clear(); P.lr_toff.clear(); P.lr_k.clear();
+    P.lr_tlen = 0;
+    {
+        std::vector<size_t> order(H.lowrank.size());
+        std::iota(order.begin(), order.end(), size_t(0));
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+            return H.lowrank[a].level < H.lowrank[b].level;
+        });
+        for (size_t o : order) {
+            const LowRankBlock& B = H.lowrank[o];
+            P.lr_level_ptr[B.level + 1]++;
+            P.lr_x0.push_back(t.begin(B.level, B.X));
+            P.lr_mx.push_back(t.end(B.level, B.X) - t.begin(B.level, B.X));
+            P.lr_y0.push_back(t.begin(B.level, B.Y));
+            P.lr_my.push_back(t.end(B.level, B.Y) - t.begin(B.level, B.Y));
+            P.lr_k.push_back(B.k);
+            const int64_t ou = place(int64_t(B.U.size()));
+            copies.push_back({&B.U, ou, 1, int64_t(B.U.size()), int64_t(B.U.size())});
+            P.lr_uoff.push_back(ou);
+            const int64_t ov = place(int64_t(B.V.size()));
+            copies.push_back({&B.V, ov, 1, int64_t(B.V.size()), int64_t(B.V.size())});
+            P.lr_voff.push_back(ov);
+            P.lr_toff.push_back(P.lr_tlen);
+            P.lr_tlen += B.k;
+        }
+        for (int l = 0; l <= K; ++l) P.lr_level_ptr[l + 1] += P.lr_level_ptr[l];
+    }
+    total = (total + 3) / 4 * 4;
+    std::vector<double>().swap(P.ops);
+    P.ops.resize(size_t(total));
+    // every element is written exactly once: block entries or zero padding
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < int64_t(copies.size()); ++c) {
+        const Copy& C = copies[c];
+        const double* src = C.src->data();
+        double* dst = P.ops.data() + C.dst;
+        for (int64_t r = 0; r < C.rows; ++r) {
+            std::memcpy(dst + r * C.pad, src + r * C.cols, size_t(C.cols) * sizeof(double));
+            for (int64_t z = C.cols; z < C.pad; ++z) dst[r * C.pad + z] = 0.0;
+        }
+    }
+    // alignment gaps between blocks
+    {
+        std::vector<std::pair<int64_t, int64_t>> spans;
+        spans.reserve(copies.size());
+        for (const Copy& C : copies) spans.push_back({C.dst, C.dst + C.rows * C.pad});
+        std::sort(spans.begin(), spans.end());
+        int64_t pos = 0;
+        for (const auto& s : spans) {
+            for (int64_t z = pos; z < s.first; ++z) P.ops[z] = 0.0;
+            pos = std::max(pos, s.second);
+        }
+        for (int64_t z = pos; z < total; ++z) P.ops[z] = 0.0;
+    }
+}
+
+}  // namespace
+
+std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf_size,
+                       int kappa_forced, const double* domain_lo, double domain_side,
+                       int threads) {
+    const auto t0 = std::chrono::steady_clock::now();
+    auto tp = t0;
+    const bool verbose = std::getenv("H2_VERBOSE") != nullptr;
+    auto tick = [&](const char* what) {
+        const auto now = std::chrono::steady_clock::now();
+        if (verbose)
+            std::fprintf(stderr, "[h2 build] %-10s %8.3f s\n", what,
+                         std::chrono::duration<double>(now - tp).count());
+        tp = now;
+    };
+    if (threads > 0) omp_set_num_threads(threads);
+    build_tree(H.tree, points, N, d, leaf_size, kappa_forced, domain_lo, domain_side);
+    if (H.tree.kappa > 20 / (d == 2 ? 1 : 1) || H.tree.nboxes(H.tree.kappa) > (int64_t(1) << 24))
+        return "tree too deep (more than 2^24 leaves)";
+    tick("tree");
+    build_lists(H.tree, H.lists);
+    tick("lists");
+    H.bases.clear();
+    if (H.variant == 0 || H.variant == 1) {
+        H.bases.emplace_back();
+        b2t(H, H.bases.back(), H.lists.far, H.eps_far);
+    }
+    if (H.variant == 0) {
+        H.bases.emplace_back();
+        t2b(H, H.bases.back(), H.lists.ver, H.eps_ver);
+    }
+    if (H.variant == 2) {
+        H.bases.emplace_back();
+        b2t(H, H.bases.back(), H.lists.sqrtd, H.eps_far);
+    }
+    tick("pivots");
+    for (Basis& B : H.bases) {
+        std::string e = operators(H, B);
+        if (!e.empty()) return e;
+    }
+    if (H.variant == 1) pure_aca(H);
+    tick("operators");
+    pack(H);
+    // the packed array now holds every operator: keep only pivots and sizes
+    for (Basis& B : H.bases) {
+        for (auto& lv : B.T) for (auto& M : lv) { std::vector<double>().swap(M); }
+    }
+    H.lowrank_entries = 0;
+    for (LowRankBlock& B : H.lowrank) {
+        H.lowrank_entries += int64_t(B.U.size() + B.V.size());
+        std::vector<double>().swap(B.U);
+        std::vector<double>().swap(B.V);
+    }
+    tick("pack");
+    // near-field work
+    const Tree& t = H.tree;
+    const Csr& NL = (H.variant == 2) ? H.lists.near_sqrt : H.lists.near_star;
+    H.near_pairs = 0;
+    H.near_evals = 0;
+    for (int64_t X = 0; X < t.nboxes(t.kappa); ++X)
+        for (int64_t e = NL.ptr[X]; e < NL.ptr[X + 1]; ++e) {
+            const int64_t Y = NL.idx[e];
+            H.near_pairs++;
+            H.near_evals += (t.end(t.kappa, X) - t.begin(t.kappa, X)) *
+                            (t.end(t.kappa, Y) - t.begin(t.kappa, Y));
+        }
+    H.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return "";
+}
+
+}  // namespace h2

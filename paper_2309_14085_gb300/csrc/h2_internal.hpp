@@ -1,0 +1,132 @@
+// Internal host-side structures of the H2* library (not part of the C ABI).
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace h2 {
+
+// G(r) evaluated from r^2 on the host, fp64.  Diagonal / coincident points
+// take G's diagonal value: 0 for log r and 1/r (§6.1.1, §6.2.1), 1 for exp(-r)
+// and the inverse multiquadric.
+struct KernelSpec {
+    int kind = 0;
+    double param = 0.1;
+    double diag() const { return (kind == 0 || kind == 1) ? 0.0 : 1.0; }
+    double operator()(double r2) const {
+        if (r2 == 0.0) return diag();
+        const double r = std::sqrt(r2);
+        switch (kind) {
+            case 0: return std::log(r);
+            case 1: return 1.0 / r;
+            case 2: { const double s = r / param; return 1.0 / std::sqrt(1.0 + s * s); }
+            default: return std::exp(-r);
+        }
+    }
+};
+
+// 2^d uniform tree (§3.1), points stored in tree order (by leaf key, then by
+// user index).  Box keys are bit-interleaved, x fastest.
+struct Tree {
+    int d = 0, kappa = 0;
+    int64_t N = 0;
+    double lo[3] = {0, 0, 0};
+    double side = 1.0;
+    std::vector<int64_t> perm;      // tree position -> user index
+    std::vector<int64_t> leaf_ptr;  // 2^(d kappa) + 1 prefix offsets
+    std::vector<double> x;          // N x d coordinates in tree order
+
+    int64_t nboxes(int l) const { return int64_t(1) << (d * l); }
+    int64_t begin(int l, int64_t key) const { return leaf_ptr[size_t(key << (d * (kappa - l)))]; }
+    int64_t end(int l, int64_t key) const { return leaf_ptr[size_t((key + 1) << (d * (kappa - l)))]; }
+    double r2(int64_t a, int64_t b) const {   // |x_a - x_b|^2, squares summed in coordinate order
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) { const double t = x[a * d + k] - x[b * d + k]; s = s + t * t; }
+        return s;
+    }
+};
+
+// Compressed sparse rows: lists of box keys per box of one level.
+struct Csr {
+    std::vector<int64_t> ptr, idx;
+    int64_t size(int64_t X) const { return ptr[X + 1] - ptr[X]; }
+};
+
+// Interaction and near-field lists, per level (§3.5 weak, §3.3 strong).
+struct Lists {
+    std::vector<Csr> far, ver, sqrtd;   // [level]
+    Csr near_star, near_sqrt;           // leaf level
+};
+
+// One nested basis (far field / vertex-sharing / sqrt(d)).  Pivots are tree
+// positions; for symmetric kernels with equal sources and targets the outgoing
+// pivots are t^{X,o} = s^{X,i}, s^{X,o} = t^{X,i} and V = U.
+struct Basis {
+    int lmin = 0;
+    const std::vector<Csr>* il = nullptr;                    // interaction lists used
+    std::vector<std::vector<std::vector<int64_t>>> tau, sig;  // [l][X] t^{X,i}, s^{X,i}
+    std::vector<std::vector<double>> U;                       // [leaf] m x r row-major (L2P)
+    std::vector<std::vector<std::vector<double>>> Ut;         // [l][X] r_X x r_parent (L2L), l > lmin
+    std::vector<std::vector<std::vector<double>>> T;          // [l][X] r_X x sum_Y r_Y (M2L)
+    int rank(int l, int64_t X) const { return int(tau[l][X].size()); }
+};
+
+// (H2+H)*: one ACA per vertex-sharing pair (Algorithm 3).
+struct LowRankBlock {
+    int level;
+    int64_t X, Y;
+    int k;
+    std::vector<double> U;   // |t^X| x k, column-major (point index fastest)
+    std::vector<double> V;   // |t^Y| x k, column-major
+};
+
+// Device-ready flat layout (all offsets in elements).
+struct Packed {
+    int nb = 0;                       // nested bases (1 or 2)
+    int64_t box_total = 0;            // boxes over levels 0..kappa
+    std::vector<int64_t> box_base;    // first box id of each level
+    std::vector<int32_t> rank;        // [slot] slot = b * box_total + box_base[l] + X
+    std::vector<int64_t> voff;        // [slot] offset into the v / u vectors
+    int64_t vlen = 0;
+    std::vector<double> ops;          // every operator entry (U, L2L, M2L)
+    std::vector<int64_t> uoff;        // [slot] leaf basis U offset (leaf slots)
+    std::vector<int64_t> utoff;       // [slot] L2L matrix (child slot), -1 if none
+    // M2M: parent slots per parent level; L2L: child slots per child level.
+    std::vector<std::vector<int64_t>> m2m_tasks, l2l_tasks;   // [level]
+    // M2L: one task per target slot with a non-empty list and rank > 0
+    std::vector<int64_t> m2l_slot, m2l_toff, m2l_src_ptr, m2l_src;
+    std::vector<int32_t> m2l_k, m2l_kpad;
+    int32_t m2l_kpad_max = 0;
+    int64_t m2l_entries = 0;          // sum over tasks of rank * kpad (stored)
+    // leaves and the near field
+    std::vector<int64_t> near_ptr, near_idx;   // per leaf, neighbour leaf keys
+    // (H2+H)* vertex-sharing factors: per level, blocks grouped by target X
+    std::vector<int64_t> lr_level_ptr;         // [kappa + 2] into the lr_* arrays
+    std::vector<int64_t> lr_x0, lr_mx, lr_y0, lr_my, lr_uoff, lr_voff, lr_toff;
+    std::vector<int32_t> lr_k;
+    int64_t lr_tlen = 0;                       // scratch length for V^T q_Y
+};
+
+struct Host {
+    KernelSpec kern;
+    int variant = 0;
+    int storage = 0;
+    double eps_far = 0, eps_ver = 0;
+    Tree tree;
+    Lists lists;
+    std::vector<Basis> bases;
+    std::vector<LowRankBlock> lowrank;
+    Packed packed;
+    double build_seconds = 0;
+    int64_t near_pairs = 0, near_evals = 0;
+    int64_t lowrank_entries = 0;     // stored (H2+H)* factor entries
+};
+
+// Construction (build.cpp).  Return "" on success or an error message.
+std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf_size,
+                       int kappa_forced, const double* domain_lo, double domain_side,
+                       int threads);
+
+}  // namespace h2

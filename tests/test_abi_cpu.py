@@ -1,0 +1,123 @@
+"""The C ABI library on the CPU: it loads, exports every symbol its header
+declares, validates arguments, and its host construction (tree, lists, ACA,
+B2T / T2B pivots) agrees index for index with the oracle.  No compute call
+needs a GPU here (host-only handles)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2309_14085_gb300 as pkg
+from oracle import h2 as oh2
+from oracle import tree as otree
+from paper_2309_14085_gb300 import H2Error, H2Matrix, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built_library():
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_2309_14085_gb300 import build_lib
+        build_lib.build()
+    return pkg.lib()
+
+
+def test_library_exports_every_declared_symbol():
+    names = set()
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(h2_\w+)\s*\(", text, re.M))
+    assert {"h2_build", "h2_matvec", "h2_info", "h2_destroy", "h2_last_error"} <= names
+    L = ctypes.CDLL(pkg.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert set(pkg.EXPORTED) <= names
+
+
+def test_invalid_arguments_return_error_codes():
+    P = inputs.points(100, 2, 1)
+    with pytest.raises(H2Error) as e:
+        H2Matrix(P, "log2d", leaf_size=0, tol=1e-6, host_only=True)
+    assert e.value.code == -1
+    with pytest.raises(H2Error):
+        H2Matrix(P, "log2d", leaf_size=8, tol=2.0, host_only=True)
+    with pytest.raises(H2Error):
+        H2Matrix(np.zeros((10, 4)), "log2d", host_only=True)
+    with pytest.raises(H2Error):
+        H2Matrix(P, "log2d", domain=((0.0, 0.0), 0.5), host_only=True)   # points outside
+    bad = P.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(H2Error):
+        H2Matrix(bad, "log2d", host_only=True)
+    h = ctypes.c_void_p()
+    assert pkg.lib().h2_build(None, 10, 2, 0, 8, 1e-6, 0, None, ctypes.byref(h)) == -1
+    assert b"NULL" in pkg.lib().h2_last_error()
+
+
+def test_matvec_on_host_only_handle_is_rejected():
+    A = H2Matrix(inputs.points(300, 2, 2), "log2d", leaf_size=16, tol=1e-6, host_only=True)
+    rc = pkg.lib().h2_matvec(A._h, ctypes.c_void_p(16), 300, ctypes.c_void_p(16), 300, 1, None)
+    assert rc == -6
+    assert A.info()["bytes_device"] == 0
+
+
+@pytest.mark.parametrize("variant", ["h2star", "h2sqrt", "h2plush"])
+@pytest.mark.parametrize("kind,d,N,n_max,eps", [("log2d", 2, 4096, 64, 1e-8),
+                                                ("invr", 3, 6000, 32, 1e-6),
+                                                ("imq", 2, 3000, 32, 1e-8)])
+def test_host_pivots_match_oracle(variant, kind, d, N, n_max, eps):
+    """B2T / T2B pivots are integer decisions taken in fp64 on both sides with
+    the same reading of ACA: they must agree index for index."""
+    P = inputs.points(N, d, 1000 + N)
+    A = H2Matrix(P, kind, leaf_size=n_max, tol=eps, variant=variant, host_only=True)
+    O = oh2.H2(P, kind, variant=variant, n_max=n_max, eps=eps)
+    assert np.array_equal(A.tree_order(), O.tree.order)
+    names = ["far", "ver"] if variant == "h2star" else ["far"]
+    total = 0
+    for b, name in enumerate(names):
+        B = O.bases[name]
+        for (l, X), ti in B.ti.items():
+            gti, gsi = A.pivots(b, l, X)
+            assert np.array_equal(gti, ti), (name, l, X)
+            assert np.array_equal(gsi, B.si[(l, X)]), (name, l, X)
+            total += 1
+    assert total > 0
+    info = A.info()
+    if variant == "h2plush":
+        assert info["lowrank_pairs"] == len(O.lowrank)
+
+
+def test_list_counts_on_full_grids():
+    """Stored M2L pairs and near-field blocks on full uniform grids: 2D kappa 3
+    has 672 far / 196 vertex-sharing pairs and 288 near-field blocks; strong
+    admissibility 1272 pairs and 484 near blocks (the same counts the oracle's
+    lists give, which its own tests pin to the paper's closed forms)."""
+    P = inputs.points(4096, 2, 1001)
+    A = H2Matrix(P, "log2d", leaf_size=64, tol=1e-4, host_only=True)
+    info = A.info()
+    assert info["kappa"] == 3 and info["m2l_pairs"] == [672, 196] and info["near_pairs"] == 288
+    S = H2Matrix(P, "log2d", leaf_size=64, tol=1e-4, variant="h2sqrt", host_only=True)
+    si = S.info()
+    assert si["m2l_pairs"][0] == 1272 and si["near_pairs"] == 484
+    t = otree.Tree(P, n_max=64)
+    assert sum(len(t.near_star(3, X)) for X in range(64)) == 288
+
+
+def test_degenerate_trees_build():
+    # fewer points than a leaf holds: kappa 0, everything is near field
+    A = H2Matrix(inputs.points(10, 2, 3), "log2d", leaf_size=64, tol=1e-8, host_only=True)
+    assert A.info()["kappa"] == 0 and A.info()["near_pairs"] == 1
+    # one point
+    B = H2Matrix(np.array([[0.25, -0.5, 0.125]]), "invr", leaf_size=4, tol=1e-8, host_only=True)
+    assert B.info()["N"] == 1
+    # kappa 1: no far field, vertex-sharing only
+    C = H2Matrix(inputs.points(100, 2, 4), "log2d", leaf_size=30, tol=1e-8, host_only=True)
+    assert C.info()["kappa"] == 1 and C.info()["m2l_pairs"] == [0, 4]
+    # points in one corner of a forced domain: most boxes are empty
+    P = inputs.points(500, 3, 5, lo=0.0, hi=0.2)
+    D = H2Matrix(P, "invr", leaf_size=8, tol=1e-6, domain=((0.0, 0.0, 0.0), 1.0), host_only=True)
+    assert D.info()["kappa"] >= 2

@@ -1,0 +1,156 @@
+"""GPU parity: the CUDA MVP (through the C ABI) against the FP64 oracle.
+
+Two bars, both on identical seeded inputs:
+
+* element by element against the oracle's own H2* construction and MVP.  The
+  pivots agree index for index (tests/test_abi_cpu.py), so both sides apply the
+  same compressed matrix K~ and differ only by rounding: the operators come
+  from different LU implementations (pivot matrices with condition numbers
+  up to ~1/eps) and the sums run in a different order.  Measured: ~1e-12 of
+  max|phi| in fp64 (the oracle's two operator formulas already differ by that
+  much), so the fp64 bar is 1e-10 * max|phi|.  In fp32 storage every operator
+  entry and kernel value carries ~6e-8 relative rounding; the bar is
+  2e-5 * max|phi| (and 1e-5 in the 2-norm).
+* against the plain definition phi = K q: relative 2-norm error <= 10 eps,
+  full dense for N <= 32k and 1024 sampled exact rows above.  Where the
+  method itself (the oracle's K~ on the same input) already exceeds 10 eps,
+  the bar is the oracle's own error + 2 %: the kernels cannot be more accurate
+  than the representation they apply.  (At N = 4096, 2D log r, eps = 1e-8 the
+  oracle's RE is 5-33 eps depending on the seed; the paper's own 2D tables
+  reach RE / eps = 103 at N = 6.5M.)
+"""
+
+import numpy as np
+import pytest
+
+from oracle import dense, h2
+from paper_2309_14085_gb300 import H2Matrix, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-10
+F32_TOL = 2e-5
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda:0")
+
+
+def _gpu_mvp(A, q):
+    y = A.matvec(_dev(q))
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def _maxrel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _dense_bar(y, ref, exact, eps):
+    re_gpu = dense.relative_error(y, exact)
+    re_orc = dense.relative_error(ref, exact)
+    print(f"RE vs dense: gpu {re_gpu:.3e}, oracle {re_orc:.3e}, 10 eps {10 * eps:.1e}")
+    assert re_gpu <= max(10 * eps, 1.02 * re_orc)
+
+
+@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt"])
+def test_c1_2d_log_n4096_matches_oracle_and_dense(variant):
+    P = inputs.points(4096, 2, 1001)
+    q = inputs.rhs(4096, 1, 2001)
+    A = H2Matrix(P, "log2d", leaf_size=64, tol=1e-8, variant=variant)
+    y = _gpu_mvp(A, q)
+    ref = h2.H2(P, "log2d", variant=variant, n_max=64, eps=1e-8).matvec(q)
+    assert _maxrel(y, ref) <= F64_TOL
+    _dense_bar(y, ref, dense.product("log2d", P, q), 1e-8)
+
+
+@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt"])
+def test_3d_invr_ragged_matches_oracle(variant):
+    """3D, N not a power of two, leaves of varying occupancy (ragged tiles)."""
+    P = inputs.points(9000, 3, 77)
+    q = inputs.rhs(9000, 1, 78)
+    A = H2Matrix(P, "invr", leaf_size=40, tol=1e-6, variant=variant)
+    y = _gpu_mvp(A, q)
+    ref = h2.H2(P, "invr", variant=variant, n_max=40, eps=1e-6).matvec(q)
+    assert _maxrel(y, ref) <= F64_TOL
+    _dense_bar(y, ref, dense.product("invr", P, q), 1e-6)
+
+
+@pytest.mark.parametrize("kind,d", [("imq", 2), ("matern12", 3), ("imq", 3)])
+def test_other_kernels_match_oracle(kind, d):
+    N = 3000
+    P = inputs.points(N, d, 90 + d)
+    q = inputs.rhs(N, 1, 91)
+    A = H2Matrix(P, kind, leaf_size=32, tol=1e-8)
+    y = _gpu_mvp(A, q)
+    ref = h2.H2(P, kind, n_max=32, eps=1e-8).matvec(q)
+    assert _maxrel(y, ref) <= F64_TOL
+
+
+def test_multiple_rhs_equal_columnwise():
+    P = inputs.points(5000, 2, 11)
+    Q = inputs.rhs(5000, 5, 12)
+    A = H2Matrix(P, "log2d", leaf_size=32, tol=1e-8)
+    X = torch.tensor(Q, device="cuda:0")          # (N, 5) row-major: the binding re-lays it
+    Y = A.matvec(X).cpu().numpy()
+    for c in range(5):
+        y = _gpu_mvp(A, Q[:, c])
+        assert np.array_equal(Y[:, c], y)
+    ref = h2.H2(P, "log2d", n_max=32, eps=1e-8).matvec(Q)
+    assert _maxrel(Y, ref) <= F64_TOL
+
+
+def test_f32_storage_against_oracle():
+    P = inputs.points(6000, 3, 21)
+    q = inputs.rhs(6000, 1, 22)
+    A = H2Matrix(P, "invr", leaf_size=32, tol=1e-6, storage="f32")
+    y = _gpu_mvp(A, q)
+    ref = h2.H2(P, "invr", n_max=32, eps=1e-6).matvec(q)
+    assert _maxrel(y, ref) <= F32_TOL
+    assert dense.relative_error(y, ref) <= 1e-5
+    _dense_bar(y, ref, dense.product("invr", P, q), 1e-6)
+
+
+def test_edge_cases_small_and_degenerate():
+    # kappa 0: a single leaf, the product is the dense near field
+    P = inputs.points(40, 2, 31)
+    q = inputs.rhs(40, 1, 32)
+    A = H2Matrix(P, "log2d", leaf_size=64, tol=1e-8)
+    assert _maxrel(_gpu_mvp(A, q), dense.product("log2d", P, q)) <= 1e-13
+    # one point: K = [0]
+    B = H2Matrix(np.array([[0.1, 0.2]]), "log2d", leaf_size=4, tol=1e-8)
+    assert _gpu_mvp(B, np.array([3.0]))[0] == 0.0
+    # kappa 1: vertex-sharing only
+    P = inputs.points(200, 2, 33)
+    q = inputs.rhs(200, 1, 34)
+    C = H2Matrix(P, "log2d", leaf_size=60, tol=1e-10)
+    ref = h2.H2(P, "log2d", n_max=60, eps=1e-10).matvec(q)
+    assert _maxrel(_gpu_mvp(C, q), ref) <= F64_TOL
+    # coincident points (r = 0 off the diagonal take the diagonal value)
+    P = inputs.points(300, 3, 35)
+    P[7] = P[100]
+    q = inputs.rhs(300, 1, 36)
+    D = H2Matrix(P, "invr", leaf_size=16, tol=1e-8)
+    ref = h2.H2(P, "invr", n_max=16, eps=1e-8).matvec(q)
+    assert _maxrel(_gpu_mvp(D, q), ref) <= F64_TOL
+    # most boxes empty: points in one corner of a forced domain
+    P = inputs.points(800, 3, 37, lo=0.0, hi=0.3)
+    q = inputs.rhs(800, 1, 38)
+    dom = (np.zeros(3), 1.0)
+    E = H2Matrix(P, "invr", leaf_size=8, tol=1e-8, domain=dom)
+    ref = h2.H2(P, "invr", n_max=8, eps=1e-8, domain=dom).matvec(q)
+    assert _maxrel(_gpu_mvp(E, q), ref) <= F64_TOL
+
+
+def test_c2_3d_invr_n262144_sampled_rows():
+    """The benchmarked workload (3D 1/r, N = 262144, octree kappa 4, eps 1e-6,
+    fp64, one RHS, the same launch configuration bench.py times): 1024 exact
+    rows of K q sampled at random."""
+    w = inputs.workload("c2_3d_invr_n262144")
+    P, q = w["points"], w["q"]
+    A = H2Matrix(P, "invr", leaf_size=64, tol=1e-6)
+    y = _gpu_mvp(A, q)
+    rows = np.random.default_rng(5).choice(P.shape[0], 1024, replace=False)
+    exact = dense.rows("invr", P, q, rows)
+    assert dense.relative_error(y[rows], exact) <= 10 * 1e-6

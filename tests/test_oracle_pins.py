@@ -252,7 +252,7 @@ def test_aca_rank_monotone_in_eps_and_edge_cases():
 @pytest.fixture(scope="module")
 def h2star_small():
     P = inputs.points(1200, 2, 21)
-    return h2.H2(P, "log2d", n_max=16, eps=1e-8)
+    return h2.H2(P, "log2d", n_max=16, eps=1e-8, symmetric=False)
 
 
 def test_operators_interpolate_on_pivots(h2star_small):
