@@ -53,8 +53,12 @@ extern "C" {
 #define H2_SQRTD_B            2   /* H2_sqrt(d)(b), App. A */
 
 /* ---- operator storage precision ------------------------------------------- */
-#define H2_F64                0   /* operators, potentials and accumulation in fp64 */
-#define H2_F32                1   /* operators and near field in fp32, fp32 accumulate */
+#define H2_F64                0   /* operators, coefficients and accumulation in fp64 (FP64 pipe) */
+#define H2_F32                1   /* operators and near field in fp32, fp32 accumulate          */
+#define H2_DF64               2   /* double-float: every fp64 operator entry and coefficient is
+                                     kept as a pair of floats (hi + lo, 48-bit significand) and
+                                     multiplied / accumulated with error-free transformations
+                                     on the FP32 pipe (near field from stored blocks)           */
 
 /* Optional build settings; pass NULL for all defaults.  Zero-initialise and
  * set the fields you need: every zero field means "default". */
@@ -72,6 +76,9 @@ typedef struct {
                               h2_info / h2_get_pivots work, h2_matvec returns
                               H2_E_NO_DEVICE                                        */
     double kparam;         /* kernel parameter (IMQ c; default 0.1)                    */
+    int    near_mode;      /* near field: 0 default (stored blocks for H2_F64 / H2_DF64,
+                              on the fly from the coordinates for H2_F32), 1 on the fly,
+                              2 stored kernel blocks (with L2P fused into them)       */
 } h2_build_opts;
 
 typedef struct h2_handle_s* h2_handle;
@@ -111,8 +118,9 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size,
  *
  * Every step runs in this library's CUDA kernels: gather into tree order,
  * P2M, M2M, M2L (far and vertex-sharing), L2L, L2P fused with the near field
- * evaluated on the fly from the coordinates, scatter back.  Precision follows
- * the build's storage (fp64, or fp32 with fp32 accumulation).
+ * (evaluated on the fly from the coordinates, or from stored kernel blocks,
+ * per h2_build_opts.near_mode), scatter back.  Precision follows the build's
+ * storage (H2_F64, H2_F32 or H2_DF64).
  * Errors: H2_E_INVALID_ARG, H2_E_NO_DEVICE (host-only handle), H2_E_CUDA.
  */
 int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
@@ -134,6 +142,10 @@ typedef struct {
     int64_t m2l_src_coeffs;        /* M2L: source coefficients gathered, summed over targets */
     int64_t m2l_dst_coeffs;        /* M2L: target coefficients written                     */
     int64_t vlen;                  /* multipole (= local) coefficients over all clusters   */
+    int64_t bytes_leaf_rows;       /* stored near-field blocks + fused leaf bases (0 when
+                                      the near field is evaluated on the fly)               */
+    int64_t leaf_src_coeffs;       /* leaf block rows: coefficients gathered, summed        */
+    int     near_stored;           /* 1: near field from stored blocks, 0: on the fly      */
     int64_t bytes_lowrank;         /* stored (H2+H)* U, V factors                          */
     int64_t bytes_device;          /* total device bytes held by the handle                */
     int64_t alg_bytes_per_rhs;     /* algorithmic HBM bytes of one MVP with one RHS      */

@@ -83,8 +83,12 @@ class H2:
     """A compressed representation K~ of the kernel matrix of points P."""
 
     def __init__(self, P, kind, variant="h2star", n_max=64, eps=1e-8, eps_far=None,
-                 eps_ver=None, param=0.1, kappa=None, domain=None, symmetric=True):
+                 eps_ver=None, param=0.1, kappa=None, domain=None, symmetric=True,
+                 store_m2l=True):
         self.P = np.asarray(P, dtype=np.float64)
+        # M2L T_{X,Y} = K_{t^{X,i}, s^{Y,o}} is a plain kernel block (§3.6.4): with
+        # store_m2l=False it is evaluated when applied instead of being kept.
+        self.store_m2l = store_m2l
         # Remark after §3.6.4: for a symmetric kernel matrix the P2M / M2M
         # operators are the transposes of the L2P / L2L operators.  With
         # symmetric=False they are formed from their own formulas instead.
@@ -192,10 +196,11 @@ class H2:
                                                   lu_i[(l, X)])
                     b.Vt[(l + 1, c)] = b.Ut[(l + 1, c)].T if self.symmetric else \
                         _left_inv(lu_o[(l, X)], self.K(b.to[(l, X)], b.so[(l + 1, c)]))
-        for l in range(b.lmin, K + 1):
-            for X in range(t.nboxes(l)):
-                for Y in b.il[(l, X)]:
-                    b.T[(l, X, Y)] = self.K(b.ti[(l, X)], b.so[(l, Y)])
+        if self.store_m2l:
+            for l in range(b.lmin, K + 1):
+                for X in range(t.nboxes(l)):
+                    for Y in b.il[(l, X)]:
+                        b.T[(l, X, Y)] = self.K(b.ti[(l, X)], b.so[(l, Y)])
 
     # ---- the MVP (§5.1.2, §5.2.2, App. A.2) -------------------------------------
     def matvec(self, q):
@@ -234,7 +239,8 @@ class H2:
             for X in range(t.nboxes(l)):
                 acc = np.zeros((b.rank(l, X),) + q.shape[1:])
                 for Y in b.il[(l, X)]:
-                    acc += b.T[(l, X, Y)] @ v[(l, Y)]
+                    T = b.T[(l, X, Y)] if self.store_m2l else self.K(b.ti[(l, X)], b.so[(l, Y)])
+                    acc += T @ v[(l, Y)]
                 u[(l, X)] = acc
         # downward traversal: L2L at lmin .. kappa-1, L2P at the leaves
         for l in range(b.lmin, K):

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libh2star.so")
 
 KERNELS = {"log2d": 0, "invr": 1, "imq": 2, "matern12": 3}
 VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2}
-STORAGE = {"f64": 0, "f32": 1}
+STORAGE = {"f64": 0, "f32": 1, "df64": 2}
+NEAR = {None: 0, "fly": 1, "stored": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
 EXPORTED = ("h2_build", "h2_matvec", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy")
@@ -32,7 +33,8 @@ class BuildOpts(ctypes.Structure):
                 ("storage", ctypes.c_int), ("kappa", ctypes.c_int),
                 ("use_domain", ctypes.c_int), ("domain_lo", ctypes.c_double * 3),
                 ("domain_side", ctypes.c_double), ("threads", ctypes.c_int),
-                ("host_only", ctypes.c_int), ("kparam", ctypes.c_double)]
+                ("host_only", ctypes.c_int), ("kparam", ctypes.c_double),
+                ("near_mode", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -46,6 +48,8 @@ class Stats(ctypes.Structure):
                 ("bytes_basis", ctypes.c_int64), ("bytes_transfer", ctypes.c_int64),
                 ("bytes_m2l", ctypes.c_int64), ("m2l_src_coeffs", ctypes.c_int64),
                 ("m2l_dst_coeffs", ctypes.c_int64), ("vlen", ctypes.c_int64),
+                ("bytes_leaf_rows", ctypes.c_int64), ("leaf_src_coeffs", ctypes.c_int64),
+                ("near_stored", ctypes.c_int),
                 ("bytes_lowrank", ctypes.c_int64),
                 ("bytes_device", ctypes.c_int64), ("alg_bytes_per_rhs", ctypes.c_int64),
                 ("build_seconds", ctypes.c_double)]
@@ -104,7 +108,7 @@ class H2Matrix:
 
     def __init__(self, points, kernel, leaf_size=64, tol=1e-8, variant="h2star", storage="f64",
                  eps_far=None, eps_ver=None, kappa=None, domain=None, threads=0,
-                 host_only=False, kparam=None):
+                 host_only=False, kparam=None, near=None):
         P = np.ascontiguousarray(points, dtype=np.float64)
         if P.ndim != 2:
             raise ValueError("points must be N x d")
@@ -124,6 +128,7 @@ class H2Matrix:
         o.threads = threads
         o.host_only = int(host_only)
         o.kparam = kparam or 0.0
+        o.near_mode = NEAR[near]
         h = ctypes.c_void_p()
         _check(lib().h2_build(P.ctypes.data, self.N, self.d, KERNELS[kernel], leaf_size, tol,
                               VARIANTS[variant], ctypes.byref(o), ctypes.byref(h)))

@@ -37,20 +37,25 @@ enum Stage { ST_GATHER, ST_P2M, ST_M2M, ST_M2L, ST_L2L, ST_LEAF, ST_LOWRANK, ST_
 
 }  // namespace
 
+// Device copy of one block-row task list.
+struct DevRowTasks {
+    int64_t n = 0;
+    size_t smem = 0;
+    int64_t *dst = nullptr, *aoff = nullptr, *seg_ptr = nullptr, *seg_off = nullptr;
+    int32_t *rows = nullptr, *kpad = nullptr, *seg_len = nullptr;
+};
+
 struct h2_handle_s {
     h2::Host host;
     bool on_device = false;
     int device = -1;
-    size_t tsize = 8;             // sizeof storage type
+    size_t vsize = 8;             // sizeof coefficient type
     int64_t bytes_device = 0;
     // device buffers
-    void* ops = nullptr;          // T
-    void* xs = nullptr;           // T, d x N
-    void* q = nullptr;            // T, N
-    void* phi = nullptr;          // T, N
-    void* v = nullptr;            // T, vlen
-    void* u = nullptr;            // T, vlen
-    void* lr_t = nullptr;         // T, lr_tlen
+    void* ops = nullptr;          // stored entries (double / float / float2)
+    void* xs = nullptr;           // coordinates, d x N (on-the-fly near field)
+    void* vec = nullptr;          // [ q | v | u | phi ]
+    void* lr_t = nullptr;         // (H2+H)* scratch V^T q_Y
     int64_t* perm = nullptr;
     int64_t* leaf_ptr = nullptr;
     int64_t* near_ptr = nullptr;
@@ -58,17 +63,13 @@ struct h2_handle_s {
     int32_t* rank = nullptr;
     int64_t* voff = nullptr;
     int64_t* uoff = nullptr;
+    int32_t* ustride = nullptr;
     int64_t* utoff = nullptr;
     int64_t* m2m_tasks = nullptr;  // all levels concatenated
     int64_t* l2l_tasks = nullptr;
     std::vector<int64_t> m2m_lptr, l2l_lptr;   // host offsets per level
-    int64_t* m2l_slot = nullptr;
-    int64_t* m2l_toff = nullptr;
-    int32_t* m2l_kpad = nullptr;
-    int64_t* m2l_src_ptr = nullptr;
-    int64_t* m2l_src = nullptr;
-    int64_t m2l_ntask = 0;
-    size_t m2l_smem = 0;
+    size_t m2m_smem = 0;
+    DevRowTasks m2l, leaf;
     // (H2+H)*
     int64_t *lr_y0 = nullptr, *lr_my = nullptr, *lr_uoff = nullptr, *lr_voff = nullptr,
             *lr_toff = nullptr, *lr_x0 = nullptr, *lr_mx = nullptr, *lr_gptr = nullptr;
@@ -85,7 +86,7 @@ struct h2_handle_s {
     cudaEvent_t* ev = nullptr;          // current set
     double stage_ms[ST_N] = {};
     int64_t stage_calls = 0;
-    int64_t launches = 0;               // kernels launched by h2_matvec (all calls)
+    int64_t launches = 0;               // kernels launched by h2_matvec
 };
 
 namespace {
@@ -115,43 +116,65 @@ int dev_alloc(h2_handle h, void** dst, size_t bytes) {
     return H2_OK;
 }
 
-template <typename T>
-std::vector<T> convert(const std::vector<double>& a) {
-    return std::vector<T>(a.begin(), a.end());
-}
-
-#define H2_TRY(x)                \
-    do {                         \
-        int rc_ = (x);           \
+#define H2_TRY(x)                     \
+    do {                              \
+        int rc_ = (x);                \
         if (rc_ != H2_OK) return rc_; \
     } while (0)
 
-template <typename T>
+// Stored entry conversion from the fp64 host value.
+template <class A> struct Conv;
+template <> struct Conv<h2::F64> { static double of(double a) { return a; } };
+template <> struct Conv<h2::F32> { static float of(double a) { return float(a); } };
+template <> struct Conv<h2::DF> {
+    static float2 of(double a) {
+        const float hi = float(a);
+        return make_float2(hi, float(a - double(hi)));
+    }
+};
+
+int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize) {
+    D.n = R.size();
+    H2_TRY(dev_upload(h, &D.dst, R.dst));
+    H2_TRY(dev_upload(h, &D.aoff, R.aoff));
+    H2_TRY(dev_upload(h, &D.seg_ptr, R.seg_ptr));
+    H2_TRY(dev_upload(h, &D.seg_off, R.seg_off));
+    H2_TRY(dev_upload(h, &D.rows, R.rows));
+    H2_TRY(dev_upload(h, &D.kpad, R.kpad));
+    H2_TRY(dev_upload(h, &D.seg_len, R.seg_len));
+    D.smem = size_t(R.kpad_max) * vsize;
+    return H2_OK;
+}
+
+template <class A>
 int upload(h2_handle h) {
+    using S = typename A::S;
+    using V = typename A::V;
     const h2::Host& H = h->host;
     const h2::Packed& P = H.packed;
     const h2::Tree& t = H.tree;
-    h->tsize = sizeof(T);
+    h->vsize = sizeof(V);
     {
-        // operators: fp64 uploads the packed array directly, fp32 converts in chunks
         void* p = nullptr;
         const size_t n = std::max<size_t>(P.ops.size(), 1);
-        H2_TRY(dev_alloc(h, &p, n * sizeof(T)));
-        if (std::is_same<T, double>::value) {
+        H2_TRY(dev_alloc(h, &p, n * sizeof(S)));
+        if (std::is_same<S, double>::value) {
             if (!P.ops.empty())
                 H2_CUDA(cudaMemcpy(p, P.ops.data(), P.ops.size() * sizeof(double), cudaMemcpyHostToDevice));
         } else {
             const size_t chunk = size_t(1) << 24;
-            std::vector<T> buf(std::min(chunk, P.ops.size()));
+            std::vector<S> buf(std::min(chunk, P.ops.size()));
             for (size_t o = 0; o < P.ops.size(); o += chunk) {
                 const size_t c = std::min(chunk, P.ops.size() - o);
-                for (size_t k = 0; k < c; ++k) buf[k] = T(P.ops[o + k]);
-                H2_CUDA(cudaMemcpy(static_cast<T*>(p) + o, buf.data(), c * sizeof(T), cudaMemcpyHostToDevice));
+#pragma omp parallel for schedule(static)
+                for (int64_t k = 0; k < int64_t(c); ++k) buf[k] = Conv<A>::of(P.ops[o + k]);
+                H2_CUDA(cudaMemcpy(static_cast<S*>(p) + o, buf.data(), c * sizeof(S), cudaMemcpyHostToDevice));
             }
         }
         h->ops = p;
     }
-    {
+    if (!P.near_stored) {
+        using T = typename std::conditional<std::is_same<A, h2::F32>::value, float, double>::type;
         std::vector<T> xs(size_t(t.d) * t.N);
         for (int64_t i = 0; i < t.N; ++i)
             for (int k = 0; k < t.d; ++k) xs[size_t(k) * t.N + i] = T(t.x[size_t(i) * t.d + k]);
@@ -159,11 +182,8 @@ int upload(h2_handle h) {
         H2_TRY(dev_upload(h, &p, xs));
         h->xs = p;
     }
-    H2_TRY(dev_alloc(h, &h->q, sizeof(T) * t.N));
-    H2_TRY(dev_alloc(h, &h->phi, sizeof(T) * t.N));
-    H2_TRY(dev_alloc(h, &h->v, sizeof(T) * std::max<int64_t>(P.vlen, 1)));
-    H2_TRY(dev_alloc(h, &h->u, sizeof(T) * std::max<int64_t>(P.vlen, 1)));
-    H2_TRY(dev_alloc(h, &h->lr_t, sizeof(T) * std::max<int64_t>(P.lr_tlen, 1)));
+    H2_TRY(dev_alloc(h, &h->vec, sizeof(V) * std::max<int64_t>(P.veclen, 1)));
+    H2_TRY(dev_alloc(h, &h->lr_t, sizeof(V) * std::max<int64_t>(P.lr_tlen, 1)));
     H2_TRY(dev_upload(h, &h->perm, t.perm));
     H2_TRY(dev_upload(h, &h->leaf_ptr, t.leaf_ptr));
     H2_TRY(dev_upload(h, &h->near_ptr, P.near_ptr));
@@ -171,6 +191,7 @@ int upload(h2_handle h) {
     H2_TRY(dev_upload(h, &h->rank, P.rank));
     H2_TRY(dev_upload(h, &h->voff, P.voff));
     H2_TRY(dev_upload(h, &h->uoff, P.uoff));
+    H2_TRY(dev_upload(h, &h->ustride, P.ustride));
     H2_TRY(dev_upload(h, &h->utoff, P.utoff));
     std::vector<int64_t> m2m, l2l;
     h->m2m_lptr.assign(t.kappa + 2, 0);
@@ -183,19 +204,19 @@ int upload(h2_handle h) {
     }
     H2_TRY(dev_upload(h, &h->m2m_tasks, m2m));
     H2_TRY(dev_upload(h, &h->l2l_tasks, l2l));
-    H2_TRY(dev_upload(h, &h->m2l_slot, P.m2l_slot));
-    H2_TRY(dev_upload(h, &h->m2l_toff, P.m2l_toff));
-    H2_TRY(dev_upload(h, &h->m2l_kpad, P.m2l_kpad));
-    H2_TRY(dev_upload(h, &h->m2l_src_ptr, P.m2l_src_ptr));
-    H2_TRY(dev_upload(h, &h->m2l_src, P.m2l_src));
-    h->m2l_ntask = int64_t(P.m2l_slot.size());
-    h->m2l_smem = size_t(P.m2l_kpad_max) * sizeof(T);
-    if (h->m2l_smem > 48 * 1024) {
-        if (h->m2l_smem > 227 * 1024)
-            return fail(H2_E_UNSUPPORTED, "M2L source coefficients exceed shared memory (ranks too high)");
-        H2_CUDA(cudaFuncSetAttribute(h2::k_m2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(h->m2l_smem)));
-    }
+    h->m2m_smem = size_t(8) * std::max(P.rank_max, 1) * sizeof(V);
+    H2_TRY(upload_rows(h, h->m2l, P.m2l, sizeof(V)));
+    H2_TRY(upload_rows(h, h->leaf, P.leaf, sizeof(V)));
+    const size_t smem_cap = 227 * 1024;
+    const size_t rows_smem = std::max(h->m2l.smem, h->leaf.smem);
+    if (rows_smem > smem_cap || h->m2m_smem > smem_cap)
+        return fail(H2_E_UNSUPPORTED, "coefficients of one block row exceed shared memory (ranks too high)");
+    if (rows_smem > 48 * 1024)
+        H2_CUDA(cudaFuncSetAttribute(h2::k_rowgemv<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(rows_smem)));
+    if (h->m2m_smem > 48 * 1024)
+        H2_CUDA(cudaFuncSetAttribute(h2::k_m2m<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(h->m2m_smem)));
     // (H2+H)* groups: consecutive blocks of one level with the same target box
     const int64_t nblk = int64_t(P.lr_k.size());
     h->lr_gptr_host.clear();
@@ -232,10 +253,11 @@ void launch_leaf(h2_handle h, cudaStream_t s) {
     const h2::Tree& t = H.tree;
     const h2::Packed& P = H.packed;
     const int64_t nleaf = t.nboxes(t.kappa);
-    h2::k_leaf<T, D, KIND><<<unsigned(nleaf), 128, 0, s>>>(
+    const T* vec = static_cast<const T*>(h->vec);
+    h2::k_leaf_fly<T, D, KIND><<<unsigned(nleaf), 128, 0, s>>>(
         nleaf, P.nb, P.box_total, P.box_base[t.kappa], h->leaf_ptr, h->near_ptr, h->near_idx,
-        h->rank, h->voff, h->uoff, static_cast<const T*>(h->ops), static_cast<const T*>(h->u),
-        static_cast<const T*>(h->xs), t.N, static_cast<const T*>(h->q), static_cast<T*>(h->phi),
+        h->rank, h->voff, h->uoff, h->ustride, static_cast<const T*>(h->ops), vec + P.u_base,
+        static_cast<const T*>(h->xs), t.N, vec + P.q_base, static_cast<T*>(h->vec) + P.phi_base,
         T(H.kern.param), T(H.kern.diag()));
 }
 
@@ -247,6 +269,14 @@ void launch_leaf_d(h2_handle h, cudaStream_t s) {
         case 2: launch_leaf<T, D, 2>(h, s); break;
         default: launch_leaf<T, D, 3>(h, s); break;
     }
+}
+
+template <class A>
+void launch_rows(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s) {
+    if (R.n == 0) return;
+    h2::k_rowgemv<A><<<unsigned(R.n), 256, R.smem, s>>>(
+        R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len,
+        static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec));
 }
 
 void mark(h2_handle h, cudaStream_t s, int stage) {
@@ -286,93 +316,110 @@ int next_event_set(h2_handle h) {
 }
 
 // One right-hand side: X, Y are single device columns (user order, fp64).
-template <typename T>
+template <class A>
 int matvec_one(h2_handle h, const double* X, double* Y, cudaStream_t s) {
+    using V = typename A::V;
+    using S = typename A::S;
     const h2::Host& H = h->host;
     const h2::Tree& t = H.tree;
     const h2::Packed& P = H.packed;
     const int K = t.kappa, d = t.d;
-    const T* ops = static_cast<const T*>(h->ops);
-    T* q = static_cast<T*>(h->q);
-    T* phi = static_cast<T*>(h->phi);
-    T* v = static_cast<T*>(h->v);
-    T* u = static_cast<T*>(h->u);
+    const S* ops = static_cast<const S*>(h->ops);
+    V* vec = static_cast<V*>(h->vec);
+    V* q = vec + P.q_base;
+    V* v = vec + P.v_base;
+    V* u = vec + P.u_base;
+    V* phi = vec + P.phi_base;
     const int64_t nleaf = t.nboxes(K);
-
     int64_t& nl = h->launches;
+
     mark(h, s, ST_GATHER);
     ++nl;
-    h2::k_gather<T><<<nblocks(t.N, 256), 256, 0, s>>>(X, h->perm, q, t.N);
+    h2::k_gather<A><<<nblocks(t.N, 256), 256, 0, s>>>(X, h->perm, q, t.N);
     mark(h, s, ST_P2M);
     if (P.nb > 0 && P.vlen > 0) {
         const int64_t ntask = P.nb * nleaf;
         ++nl;
-        h2::k_p2m<T><<<nblocks(ntask * 32, 256), 256, 0, s>>>(
-            ntask, nleaf, P.box_total, P.box_base[K], h->leaf_ptr, h->rank, h->voff, h->uoff, ops, q, v);
+        h2::k_p2m<A><<<nblocks(ntask * 32, 256), 256, 0, s>>>(
+            ntask, nleaf, P.box_total, P.box_base[K], h->leaf_ptr, h->rank, h->voff, h->uoff,
+            h->ustride, ops, q, v);
     }
     mark(h, s, ST_M2M);
     for (int l = K - 1; l >= 1; --l) {
         const int64_t n = h->m2m_lptr[l + 1] - h->m2m_lptr[l];
         if (n == 0) continue;
         ++nl;
-        h2::k_m2m<T><<<nblocks(n * 32, 256), 256, 0, s>>>(
+        h2::k_m2m<A><<<unsigned(n), 256, h->m2m_smem, s>>>(
             h->m2m_tasks + h->m2m_lptr[l], n, P.box_total, P.box_base[l], P.box_base[l + 1], 1 << d,
             h->rank, h->voff, h->utoff, ops, v);
     }
     mark(h, s, ST_M2L);
-    if (P.vlen > 0) cudaMemsetAsync(u, 0, sizeof(T) * P.vlen, s);
-    if (h->m2l_ntask > 0) {
+    if (P.vlen > 0) cudaMemsetAsync(u, 0, sizeof(V) * P.vlen, s);
+    if (h->m2l.n > 0) {
         ++nl;
-        h2::k_m2l<T><<<unsigned(h->m2l_ntask), 256, h->m2l_smem, s>>>(
-            h->m2l_ntask, h->m2l_slot, h->m2l_toff, h->m2l_kpad, h->m2l_src_ptr, h->m2l_src, h->rank,
-            h->voff, ops, v, u);
+        launch_rows<A>(h->m2l, ops, vec, s);
     }
     mark(h, s, ST_L2L);
     for (int l = 2; l <= K; ++l) {
         const int64_t n = h->l2l_lptr[l + 1] - h->l2l_lptr[l];
         if (n == 0) continue;
         ++nl;
-        h2::k_l2l<T><<<nblocks(n * 32, 256), 256, 0, s>>>(
+        h2::k_l2l<A><<<unsigned(n), 128, 0, s>>>(
             h->l2l_tasks + h->l2l_lptr[l], n, P.box_total, P.box_base[l], P.box_base[l - 1], d,
             h->rank, h->voff, h->utoff, ops, u);
     }
     mark(h, s, ST_LEAF);
-    ++nl;
-    if (d == 2) launch_leaf_d<T, 2>(h, s);
-    else launch_leaf_d<T, 3>(h, s);
-    mark(h, s, ST_LOWRANK);
-    if (H.variant == H2_PLUS_H_STAR && P.lr_tlen > 0) {
-        T* tt = static_cast<T*>(h->lr_t);
-        cudaMemsetAsync(tt, 0, sizeof(T) * P.lr_tlen, s);
-        const int chunk = 4096;
-        for (int l = 1; l <= K; ++l) {
-            const int64_t b0 = P.lr_level_ptr[l], nb = P.lr_level_ptr[l + 1] - b0;
-            if (nb == 0) continue;
-            const int64_t maxmy = h->lr_maxm_level[2 * l + 1];
-            for (int64_t off = 0; off < nb; off += 65535) {
-                const int64_t cnt = std::min<int64_t>(65535, nb - off);
-                dim3 grid(nblocks(maxmy, chunk), unsigned(cnt));
-                ++nl;
-                h2::k_lr_vtq<T><<<grid, 256, 0, s>>>(b0 + off, cnt, h->lr_y0, h->lr_my, h->lr_k, h->lr_voff,
-                                                     h->lr_toff, ops, q, tt, chunk);
-            }
+    if (P.near_stored) {
+        // empty leaves keep phi = 0: clear once, the block rows overwrite the rest
+        cudaMemsetAsync(phi, 0, sizeof(V) * t.N, s);
+        if (h->leaf.n > 0) {
+            ++nl;
+            launch_rows<A>(h->leaf, ops, vec, s);
         }
-        for (int l = 1; l <= K; ++l) {
-            const int64_t g0 = h->lr_level_gptr[l], ng = h->lr_level_gptr[l + 1] - g0;
-            if (ng == 0) continue;
-            const int64_t maxmx = h->lr_maxm_level[2 * l];
-            for (int64_t off = 0; off < ng; off += 65535) {
-                const int64_t cnt = std::min<int64_t>(65535, ng - off);
-                dim3 grid(nblocks(maxmx, 256), unsigned(cnt));
-                ++nl;
-                h2::k_lr_ut<T><<<grid, 256, 0, s>>>(g0 + off, cnt, h->lr_gptr, h->lr_x0, h->lr_mx, h->lr_k,
-                                                    h->lr_uoff, h->lr_toff, ops, tt, phi);
+    } else if constexpr (!std::is_same<A, h2::DF>::value) {
+        using T = typename A::V;
+        ++nl;
+        if (d == 2) launch_leaf_d<T, 2>(h, s);
+        else launch_leaf_d<T, 3>(h, s);
+    }
+    mark(h, s, ST_LOWRANK);
+    if constexpr (!std::is_same<A, h2::DF>::value) {
+        using T = typename A::V;
+        if (H.variant == H2_PLUS_H_STAR && P.lr_tlen > 0) {
+            T* tt = static_cast<T*>(h->lr_t);
+            cudaMemsetAsync(tt, 0, sizeof(T) * P.lr_tlen, s);
+            const int chunk = 4096;
+            for (int l = 1; l <= K; ++l) {
+                const int64_t b0 = P.lr_level_ptr[l], nb = P.lr_level_ptr[l + 1] - b0;
+                if (nb == 0) continue;
+                const int64_t maxmy = h->lr_maxm_level[2 * l + 1];
+                for (int64_t off = 0; off < nb; off += 65535) {
+                    const int64_t cnt = std::min<int64_t>(65535, nb - off);
+                    dim3 grid(nblocks(maxmy, chunk), unsigned(cnt));
+                    ++nl;
+                    h2::k_lr_vtq<T><<<grid, 256, 0, s>>>(b0 + off, cnt, h->lr_y0, h->lr_my, h->lr_k,
+                                                         h->lr_voff, h->lr_toff,
+                                                         reinterpret_cast<const T*>(ops), q, tt, chunk);
+                }
+            }
+            for (int l = 1; l <= K; ++l) {
+                const int64_t g0 = h->lr_level_gptr[l], ng = h->lr_level_gptr[l + 1] - g0;
+                if (ng == 0) continue;
+                const int64_t maxmx = h->lr_maxm_level[2 * l];
+                for (int64_t off = 0; off < ng; off += 65535) {
+                    const int64_t cnt = std::min<int64_t>(65535, ng - off);
+                    dim3 grid(nblocks(maxmx, 256), unsigned(cnt));
+                    ++nl;
+                    h2::k_lr_ut<T><<<grid, 256, 0, s>>>(g0 + off, cnt, h->lr_gptr, h->lr_x0, h->lr_mx,
+                                                        h->lr_k, h->lr_uoff, h->lr_toff,
+                                                        reinterpret_cast<const T*>(ops), tt, phi);
+                }
             }
         }
     }
     mark(h, s, ST_SCATTER);
     ++nl;
-    h2::k_scatter<T><<<nblocks(t.N, 256), 256, 0, s>>>(phi, h->perm, Y, t.N);
+    h2::k_scatter<A><<<nblocks(t.N, 256), 256, 0, s>>>(phi, h->perm, Y, t.N);
     mark(h, s, ST_N);
     H2_CUDA(cudaGetLastError());
     return H2_OK;
@@ -399,7 +446,13 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     h2_build_opts o;
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    if (o.storage != H2_F64 && o.storage != H2_F32) return fail(H2_E_INVALID_ARG, "unknown storage");
+    if (o.storage != H2_F64 && o.storage != H2_F32 && o.storage != H2_DF64)
+        return fail(H2_E_INVALID_ARG, "unknown storage");
+    if (o.near_mode < 0 || o.near_mode > 2) return fail(H2_E_INVALID_ARG, "unknown near_mode");
+    if (o.storage == H2_DF64 && o.near_mode == 1)
+        return fail(H2_E_UNSUPPORTED, "df64 storage evaluates the near field from stored blocks only");
+    if (o.storage == H2_DF64 && variant == H2_PLUS_H_STAR)
+        return fail(H2_E_UNSUPPORTED, "(H2+H)* is built for fp64 and fp32 storage");
     if (o.kappa < 0 || o.kappa > 20) return fail(H2_E_INVALID_ARG, "kappa out of range");
     if (o.eps_far < 0 || o.eps_far >= 1 || o.eps_ver < 0 || o.eps_ver >= 1)
         return fail(H2_E_INVALID_ARG, "eps_far / eps_ver must be in [0, 1)");
@@ -427,6 +480,7 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     H.kern.param = o.kparam > 0 ? o.kparam : 0.1;
     H.variant = variant;
     H.storage = o.storage;
+    H.near_mode = o.near_mode;
     H.eps_far = o.eps_far > 0 ? o.eps_far : tol;
     H.eps_ver = o.eps_ver > 0 ? o.eps_ver : tol;
     try {
@@ -443,7 +497,9 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
             return fail(H2_E_NO_DEVICE, "no CUDA device");
         }
         H2_CUDA(cudaGetDevice(&h->device));
-        int rc = (o.storage == H2_F64) ? upload<double>(h.get()) : upload<float>(h.get());
+        int rc = (o.storage == H2_F64)   ? upload<h2::F64>(h.get())
+                 : (o.storage == H2_F32) ? upload<h2::F32>(h.get())
+                                         : upload<h2::DF>(h.get());
         if (rc != H2_OK) {
             h2_destroy(h.release());
             return rc;
@@ -471,7 +527,10 @@ int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
             int rc = next_event_set(h);
             if (rc != H2_OK) return rc;
         }
-        int rc = (h->tsize == 8) ? matvec_one<double>(h, x, y, s) : matvec_one<float>(h, x, y, s);
+        const int st = h->host.storage;
+        int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, x, y, s)
+                 : (st == H2_F32) ? matvec_one<h2::F32>(h, x, y, s)
+                                  : matvec_one<h2::DF>(h, x, y, s);
         if (rc != H2_OK) return rc;
     }
     return H2_OK;
@@ -510,7 +569,7 @@ int h2_info(h2_handle h, h2_stats* st) {
         for (int l = B.lmin; l <= t.kappa; ++l) pairs += int64_t((*B.il)[l].idx.size());
         st->m2l_pairs[b] = pairs;
     }
-    const int64_t ts = H.storage == H2_F64 ? 8 : 4;
+    const int64_t ts = H.storage == H2_F32 ? 4 : 8;
     int64_t nbasis = 0, ntrans = 0, nlr = 0;
     for (const auto& B : H.bases) {
         for (const auto& U : B.U) nbasis += int64_t(U.size());
@@ -520,21 +579,24 @@ int h2_info(h2_handle h, h2_stats* st) {
     nlr = H.lowrank_entries;
     st->bytes_basis = nbasis * ts;
     st->bytes_transfer = ntrans * ts;
-    st->bytes_m2l = P.m2l_entries * ts;
-    for (size_t k = 0; k < P.m2l_slot.size(); ++k) {
-        st->m2l_src_coeffs += P.m2l_kpad[k];
-        st->m2l_dst_coeffs += P.rank[P.m2l_slot[k]];
-    }
+    st->bytes_m2l = P.m2l.entries * ts;
+    st->m2l_src_coeffs = P.m2l.src_coeffs;
+    st->m2l_dst_coeffs = P.m2l.dst_coeffs;
+    st->bytes_leaf_rows = P.leaf.entries * ts;
+    st->leaf_src_coeffs = P.leaf.src_coeffs;
+    st->near_stored = P.near_stored;
     st->vlen = P.vlen;
     st->bytes_lowrank = nlr * ts;
     st->near_pairs = H.near_pairs;
     st->near_evals = H.near_evals;
     st->lowrank_pairs = int64_t(H.lowrank.size());
     st->bytes_device = h->bytes_device;
-    // algorithmic bytes of one MVP with one RHS: every stored operator once,
-    // coordinates for the near field, user vector in and out (fp64)
-    st->alg_bytes_per_rhs = st->bytes_basis + st->bytes_transfer + st->bytes_m2l + st->bytes_lowrank +
-                            t.N * t.d * ts + 2 * t.N * 8;
+    // algorithmic bytes of one MVP with one RHS: every stored operator once
+    // (leaf bases inside the stored block rows when the near field is stored,
+    // else the bases plus the coordinates), the user vector in and out (fp64)
+    st->alg_bytes_per_rhs = st->bytes_transfer + st->bytes_m2l + st->bytes_lowrank + 2 * t.N * 8 +
+                            (P.near_stored ? st->bytes_leaf_rows
+                                           : st->bytes_basis + t.N * t.d * (ts == 4 ? 4 : 8));
     st->build_seconds = H.build_seconds;
     return H2_OK;
 }

@@ -526,6 +526,8 @@ void pack(Host& H) {
     const int K = t.kappa, d = t.d;
     Packed& P = H.packed;
     P.nb = int(H.bases.size());
+    // near field stored as leaf block rows unless fp32 (on the fly) or asked otherwise
+    P.near_stored = H.near_mode == 2 || (H.near_mode == 0 && H.storage != 1);
     P.box_base.assign(K + 2, 0);
     for (int l = 0; l <= K; ++l) P.box_base[l + 1] = P.box_base[l] + t.nboxes(l);
     P.box_total = P.box_base[K + 1];
@@ -533,7 +535,9 @@ void pack(Host& H) {
     P.rank.assign(ns, 0);
     P.voff.assign(ns, 0);
     P.uoff.assign(ns, -1);
+    P.ustride.assign(ns, 0);
     P.utoff.assign(ns, -1);
+    P.rank_max = 0;
     auto slot = [&](int b, int l, int64_t X) { return b * P.box_total + P.box_base[l] + X; };
     int64_t vo = 0;
     for (int b = 0; b < P.nb; ++b)
@@ -543,26 +547,77 @@ void pack(Host& H) {
                 const int r = (l >= H.bases[b].lmin && l <= K) ? H.bases[b].rank(l, X) : 0;
                 P.rank[s] = r;
                 P.voff[s] = vo;
+                P.rank_max = std::max(P.rank_max, r);
                 vo += r;
             }
     P.vlen = vo;
+    P.q_base = 0;
+    P.v_base = t.N;
+    P.u_base = t.N + P.vlen;
+    P.phi_base = t.N + 2 * P.vlen;
+    P.veclen = 2 * t.N + 2 * P.vlen;
     // ---- first pass: the offset of every block (each block starts on a
-    //      multiple of 4 elements), then one allocation and a parallel copy
+    //      multiple of 4 elements), then one allocation and a parallel fill
     int64_t total = 0;
     auto place = [&](int64_t n) {
         const int64_t o = (total + 3) / 4 * 4;
         total = o + n;
         return o;
     };
+    auto pad4 = [](int64_t n) { return (n + 3) / 4 * 4; };
     struct Copy { const std::vector<double>* src; int64_t dst; int64_t rows, cols, pad; };
     std::vector<Copy> copies;
-    for (int b = 0; b < P.nb; ++b) {
-        const Basis& B = H.bases[b];
-        if (K < B.lmin) continue;
-        for (int64_t X = 0; X < t.nboxes(K); ++X) {
-            const int64_t o = place(int64_t(B.U[X].size()));
-            P.uoff[slot(b, K, X)] = o;
-            copies.push_back({&B.U[X], o, 1, int64_t(B.U[X].size()), int64_t(B.U[X].size())});
+    const int64_t nleaf = t.nboxes(K);
+    const Csr& NL = (H.variant == 2) ? H.lists.near_sqrt : H.lists.near_star;
+    P.near_ptr = NL.ptr;
+    P.near_idx = NL.idx;
+    // leaf block rows: [ K(t^X, t^X') for X' in N(X) | U_X^b for each basis ]
+    P.leaf = RowTasks();
+    P.near_entries = 0;
+    std::vector<int64_t> leaf_aoff(nleaf, -1), leaf_ncols(nleaf, 0), leaf_kp(nleaf, 0);
+    if (P.near_stored) {
+        for (int64_t X = 0; X < nleaf; ++X) {
+            const int64_t m = t.leaf_ptr[X + 1] - t.leaf_ptr[X];
+            int64_t nc = 0;
+            for (int64_t e = NL.ptr[X]; e < NL.ptr[X + 1]; ++e)
+                nc += t.leaf_ptr[NL.idx[e] + 1] - t.leaf_ptr[NL.idx[e]];
+            int64_t cols = nc;
+            for (int b = 0; b < P.nb; ++b) cols += P.rank[slot(b, K, X)];
+            const int64_t kp = pad4(cols);
+            leaf_ncols[X] = nc;
+            leaf_kp[X] = kp;
+            if (m == 0) continue;
+            const int64_t o = place(m * kp);
+            leaf_aoff[X] = o;
+            P.near_entries += m * nc;
+            P.leaf.add(P.phi_base + t.leaf_ptr[X], int32_t(m), int32_t(kp), o);
+            for (int64_t e = NL.ptr[X]; e < NL.ptr[X + 1]; ++e) {
+                const int64_t Y = NL.idx[e];
+                const int64_t my = t.leaf_ptr[Y + 1] - t.leaf_ptr[Y];
+                if (my > 0) P.leaf.seg(P.q_base + t.leaf_ptr[Y], int32_t(my));
+            }
+            int64_t col = nc;
+            for (int b = 0; b < P.nb; ++b) {
+                const int64_t s = slot(b, K, X);
+                if (P.rank[s] > 0) {
+                    P.leaf.seg(P.u_base + P.voff[s], P.rank[s]);
+                    P.uoff[s] = o + col;
+                    P.ustride[s] = int32_t(kp);
+                }
+                col += P.rank[s];
+            }
+            P.leaf.close();
+        }
+    } else {
+        for (int b = 0; b < P.nb; ++b) {
+            const Basis& B = H.bases[b];
+            if (K < B.lmin) continue;
+            for (int64_t X = 0; X < nleaf; ++X) {
+                const int64_t o = place(int64_t(B.U[X].size()));
+                P.uoff[slot(b, K, X)] = o;
+                P.ustride[slot(b, K, X)] = B.rank(K, X);
+                copies.push_back({&B.U[X], o, 1, int64_t(B.U[X].size()), int64_t(B.U[X].size())});
+            }
         }
     }
     for (int b = 0; b < P.nb; ++b) {
@@ -587,15 +642,8 @@ void pack(Host& H) {
                 if (B.rank(l, X) > 0 && B.rank(l - 1, X >> d) > 0)
                     P.l2l_tasks[l].push_back(slot(b, l, X));
     }
-    // M2L: rows padded with zeros to a multiple of 4 columns
-    P.m2l_slot.clear();
-    P.m2l_toff.clear();
-    P.m2l_k.clear();
-    P.m2l_kpad.clear();
-    P.m2l_src_ptr.assign(1, 0);
-    P.m2l_src.clear();
-    P.m2l_kpad_max = 0;
-    P.m2l_entries = 0;
+    // M2L: one block row per target, rows padded with zeros to a multiple of 4
+    P.m2l = RowTasks();
     for (int b = 0; b < P.nb; ++b) {
         const Basis& B = H.bases[b];
         for (int l = B.lmin; l <= K; ++l) {
@@ -605,26 +653,18 @@ void pack(Host& H) {
                 int64_t kx = 0;
                 for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) kx += B.rank(l, L.idx[e]);
                 if (r == 0 || kx == 0) continue;
-                const int64_t kp = (kx + 3) / 4 * 4;
+                const int64_t kp = pad4(kx);
                 const int64_t o = place(int64_t(r) * kp);
-                P.m2l_slot.push_back(slot(b, l, X));
-                P.m2l_toff.push_back(o);
-                P.m2l_k.push_back(int32_t(kx));
-                P.m2l_kpad.push_back(int32_t(kp));
-                P.m2l_kpad_max = std::max<int32_t>(P.m2l_kpad_max, int32_t(kp));
-                P.m2l_entries += int64_t(r) * kp;
+                P.m2l.add(P.u_base + P.voff[slot(b, l, X)], r, int32_t(kp), o);
                 copies.push_back({&B.T[l][X], o, r, kx, kp});
                 for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
-                    const int64_t Y = L.idx[e];
-                    if (B.rank(l, Y) > 0) P.m2l_src.push_back(slot(b, l, Y));
+                    const int64_t sy = slot(b, l, L.idx[e]);
+                    if (P.rank[sy] > 0) P.m2l.seg(P.v_base + P.voff[sy], P.rank[sy]);
                 }
-                P.m2l_src_ptr.push_back(int64_t(P.m2l_src.size()));
+                P.m2l.close();
             }
         }
     }
-    const Csr& NL = (H.variant == 2) ? H.lists.near_sqrt : H.lists.near_star;
-    P.near_ptr = NL.ptr;
-    P.near_idx = NL.idx;
     // (H2+H)* factors grouped by level (blocks of one target stay consecutive)
     P.lr_level_ptr.assign(K + 2, 0);
     P.lr_x0.clear(); P.lr_mx.clear(); P.lr_y0.clear(); P.lr_my.clear();
@@ -657,30 +697,36 @@ void pack(Host& H) {
     }
     total = (total + 3) / 4 * 4;
     std::vector<double>().swap(P.ops);
-    P.ops.resize(size_t(total));
-    // every element is written exactly once: block entries or zero padding
+    P.ops.assign(size_t(total), 0.0);     // zero: padding and alignment gaps
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t c = 0; c < int64_t(copies.size()); ++c) {
         const Copy& C = copies[c];
         const double* src = C.src->data();
         double* dst = P.ops.data() + C.dst;
-        for (int64_t r = 0; r < C.rows; ++r) {
+        for (int64_t r = 0; r < C.rows; ++r)
             std::memcpy(dst + r * C.pad, src + r * C.cols, size_t(C.cols) * sizeof(double));
-            for (int64_t z = C.cols; z < C.pad; ++z) dst[r * C.pad + z] = 0.0;
-        }
     }
-    // alignment gaps between blocks
-    {
-        std::vector<std::pair<int64_t, int64_t>> spans;
-        spans.reserve(copies.size());
-        for (const Copy& C : copies) spans.push_back({C.dst, C.dst + C.rows * C.pad});
-        std::sort(spans.begin(), spans.end());
-        int64_t pos = 0;
-        for (const auto& s : spans) {
-            for (int64_t z = pos; z < s.first; ++z) P.ops[z] = 0.0;
-            pos = std::max(pos, s.second);
+    if (P.near_stored) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t X = 0; X < nleaf; ++X) {
+            if (leaf_aoff[X] < 0) continue;
+            const int64_t p0 = t.leaf_ptr[X], m = t.leaf_ptr[X + 1] - p0, kp = leaf_kp[X];
+            double* A = P.ops.data() + leaf_aoff[X];
+            for (int64_t i = 0; i < m; ++i) {
+                double* row = A + i * kp;
+                int64_t col = 0;
+                for (int64_t e = NL.ptr[X]; e < NL.ptr[X + 1]; ++e) {
+                    const int64_t Y = NL.idx[e];
+                    for (int64_t j = t.leaf_ptr[Y]; j < t.leaf_ptr[Y + 1]; ++j)
+                        row[col++] = H.kern(t.r2(p0 + i, j));
+                }
+                for (int b = 0; b < P.nb; ++b) {
+                    const int r = P.rank[slot(b, K, X)];
+                    if (r > 0) std::memcpy(row + col, H.bases[b].U[X].data() + i * r, size_t(r) * sizeof(double));
+                    col += r;
+                }
+            }
         }
-        for (int64_t z = pos; z < total; ++z) P.ops[z] = 0.0;
     }
 }
 

@@ -1,6 +1,7 @@
 // Internal host-side structures of the H2* library (not part of the C ABI).
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -82,25 +83,46 @@ struct LowRankBlock {
     std::vector<double> V;   // |t^Y| x k, column-major
 };
 
-// Device-ready flat layout (all offsets in elements).
+// Block-row GEMV tasks: y[dst + i] = sum_k A[aoff + i * kpad + k] x[k], i < rows,
+// with x the concatenation of the segments (off, len) of the coefficient buffer.
+struct RowTasks {
+    std::vector<int64_t> dst, aoff, seg_ptr{0}, seg_off;
+    std::vector<int32_t> rows, kpad, seg_len;
+    int32_t kpad_max = 0;
+    int64_t entries = 0;       // sum of rows * kpad
+    int64_t src_coeffs = 0;    // sum of kpad (coefficients gathered)
+    int64_t dst_coeffs = 0;    // sum of rows
+    void add(int64_t d, int32_t r, int32_t kp, int64_t a) {
+        dst.push_back(d); rows.push_back(r); kpad.push_back(kp); aoff.push_back(a);
+        kpad_max = std::max(kpad_max, kp);
+        entries += int64_t(r) * kp;
+        src_coeffs += kp;
+        dst_coeffs += r;
+    }
+    void seg(int64_t off, int32_t len) { seg_off.push_back(off); seg_len.push_back(len); }
+    void close() { seg_ptr.push_back(int64_t(seg_off.size())); }
+    int64_t size() const { return int64_t(dst.size()); }
+};
+
+// Device-ready flat layout (all offsets in elements).  The coefficient buffer
+// is [ q (N) | v (vlen) | u (vlen) | phi (N) ].
 struct Packed {
     int nb = 0;                       // nested bases (1 or 2)
+    int near_stored = 0;              // 1: near field stored as leaf block rows
     int64_t box_total = 0;            // boxes over levels 0..kappa
     std::vector<int64_t> box_base;    // first box id of each level
     std::vector<int32_t> rank;        // [slot] slot = b * box_total + box_base[l] + X
-    std::vector<int64_t> voff;        // [slot] offset into the v / u vectors
+    std::vector<int64_t> voff;        // [slot] offset of its v / u coefficients
     int64_t vlen = 0;
-    std::vector<double> ops;          // every operator entry (U, L2L, M2L)
-    std::vector<int64_t> uoff;        // [slot] leaf basis U offset (leaf slots)
+    int64_t q_base = 0, v_base = 0, u_base = 0, phi_base = 0, veclen = 0;
+    std::vector<double> ops;          // every operator entry
+    std::vector<int64_t> uoff;        // [slot] leaf basis U row 0 (leaf slots)
+    std::vector<int32_t> ustride;     // [slot] distance between rows of U
     std::vector<int64_t> utoff;       // [slot] L2L matrix (child slot), -1 if none
-    // M2M: parent slots per parent level; L2L: child slots per child level.
     std::vector<std::vector<int64_t>> m2m_tasks, l2l_tasks;   // [level]
-    // M2L: one task per target slot with a non-empty list and rank > 0
-    std::vector<int64_t> m2l_slot, m2l_toff, m2l_src_ptr, m2l_src;
-    std::vector<int32_t> m2l_k, m2l_kpad;
-    int32_t m2l_kpad_max = 0;
-    int64_t m2l_entries = 0;          // sum over tasks of rank * kpad (stored)
-    // leaves and the near field
+    RowTasks m2l, leaf;               // M2L targets; stored near field + L2P
+    int32_t rank_max = 0;
+    int64_t near_entries = 0;         // stored near-field kernel values
     std::vector<int64_t> near_ptr, near_idx;   // per leaf, neighbour leaf keys
     // (H2+H)* vertex-sharing factors: per level, blocks grouped by target X
     std::vector<int64_t> lr_level_ptr;         // [kappa + 2] into the lr_* arrays
@@ -113,6 +135,7 @@ struct Host {
     KernelSpec kern;
     int variant = 0;
     int storage = 0;
+    int near_mode = 0;               // 0 default, 1 on the fly, 2 stored
     double eps_far = 0, eps_ver = 0;
     Tree tree;
     Lists lists;

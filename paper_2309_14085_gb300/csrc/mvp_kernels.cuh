@@ -1,31 +1,128 @@
-// CUDA kernels of the H2* matrix-vector product (§5.1.2, §5.2.2, App. A.2),
-// templated on the storage / arithmetic type T (double or float).
+// CUDA kernels of the H2* matrix-vector product (§5.1.2, §5.2.2, App. A.2).
 //
-// Data layout (all in HBM, built once per geometry):
-//   ops      every operator entry: leaf bases U_X (m x r, row-major), L2L
-//            matrices U~_{X_c X} (r_c x r_X, row-major), M2L blocks per target
-//            [T_{X,Y1} | T_{X,Y2} | ...] (r_X x kpad, row-major, zero padded
-//            to a multiple of 4 columns), (H2+H)* factors (column-major).
-//   v, u     multipole / local coefficients of every (basis, level, box) slot.
-//   q, phi   charges / potentials in tree order (leaf-contiguous).
-//   xs       coordinates in tree order, structure of arrays (xs[k * N + i]).
+// Every kernel is templated on an arithmetic policy:
+//   F64  -- operators, coefficients and sums in IEEE double (FP64 pipe);
+//   F32  -- everything in float (FP32 pipe);
+//   DF   -- "double-float": every operator entry and coefficient is a pair
+//           (hi, lo) of floats with hi + lo equal to the fp64 value to 48
+//           significant bits, and every multiply-add runs as error-free
+//           transformations on the FP32 pipe (Dekker's product via FMA,
+//           Knuth's two-sum).  On GB300 the FP64 pipe delivers ~0.5 TFMA/s,
+//           1/73 of FP32, so fp64-grade GEMV is ALU-bound at ~4 TB/s in F64
+//           but HBM-bound in DF (about 12 FP32 operations per multiply-add).
+//
+// Data layout (HBM, built once per geometry):
+//   ops   every operator entry: leaf bases U_X, L2L matrices U~_{X_c X}
+//         (r_c x r_X row-major), block rows for M2L and the stored near field,
+//         (H2+H)* factors (column-major).
+//   vec   one coefficient buffer [ q (N) | v (vlen) | u (vlen) | phi (N) ]:
+//         charges and potentials in tree order (leaf-contiguous) and the
+//         multipole / local coefficients of every (basis, level, box) slot.
+//   xs    coordinates in tree order, structure of arrays (xs[k * N + i]).
+//
+// A "block row" task computes y[dst + i] = sum_k A[i * kpad + k] x[k] for
+// i < rows, where x is the concatenation of segments of `vec` (gathered into
+// shared memory) and A is stored row-major, zero padded to kpad (a multiple of
+// 4 entries, so rows start 16-byte aligned).  M2L is one task per target
+// cluster (x = the sources' multipoles, y = its local coefficients); the
+// stored near field is one task per leaf with the leaf's bases appended as
+// extra columns (x = neighbours' charges then the leaf's local coefficients),
+// so L2P is fused into it.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace h2 {
 
 constexpr int kWarp = 32;
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
+// ---------------------------------------------------------------------------
+// arithmetic policies
+struct F64 {
+    using S = double;       // stored operator entry
+    using V = double;       // coefficient / accumulator
+    using L = double2;      // one 16-byte load of stored entries
+    static constexpr int W = 2;
+    __device__ static V zero() { return 0.0; }
+    __device__ static V mac(V acc, S a, V x) { return fma(a, x, acc); }
+    __device__ static V add(V a, V b) { return a + b; }
+    __device__ static V from_double(double a) { return a; }
+    __device__ static double to_double(V a) { return a; }
+    __device__ static V shfl_xor(V a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    __device__ static S lget(const L& l, int k) { return k == 0 ? l.x : l.y; }
+};
+
+struct F32 {
+    using S = float;
+    using V = float;
+    using L = float4;
+    static constexpr int W = 4;
+    __device__ static V zero() { return 0.0f; }
+    __device__ static V mac(V acc, S a, V x) { return fmaf(a, x, acc); }
+    __device__ static V add(V a, V b) { return a + b; }
+    __device__ static V from_double(double a) { return float(a); }
+    __device__ static double to_double(V a) { return double(a); }
+    __device__ static V shfl_xor(V a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    __device__ static S lget(const L& l, int k) {
+        return k == 0 ? l.x : (k == 1 ? l.y : (k == 2 ? l.z : l.w));
+    }
+};
+
+struct DF {
+    using S = float2;       // (hi, lo)
+    using V = float2;
+    using L = float4;       // two entries
+    static constexpr int W = 2;
+    __device__ static V zero() { return make_float2(0.0f, 0.0f); }
+    // Knuth's two-sum of a and b, exact: s + e = a + b.
+    __device__ static void two_sum(float a, float b, float& s, float& e) {
+        s = a + b;
+        const float bb = s - a;
+        e = (a - (s - bb)) + (b - bb);
+    }
+    // acc + a * x: the product a.hi x.hi is split exactly with an FMA (Dekker),
+    // the cross terms are added in float, the sum with acc.hi is exact (two-sum).
+    __device__ static V mac(V acc, S a, V x) {
+        const float p = a.x * x.x;
+        float e = fmaf(a.x, x.x, -p);
+        e = fmaf(a.x, x.y, e);
+        e = fmaf(a.y, x.x, e);
+        float s, t;
+        two_sum(acc.x, p, s, t);
+        return make_float2(s, acc.y + (t + e));
+    }
+    __device__ static V add(V a, V b) {
+        float s, t;
+        two_sum(a.x, b.x, s, t);
+        const float lo = t + a.y + b.y;
+        const float hi = s + lo;                 // renormalise (fast two-sum)
+        return make_float2(hi, lo - (hi - s));
+    }
+    __device__ static V from_double(double a) {
+        const float hi = __double2float_rn(a);
+        return make_float2(hi, __double2float_rn(a - double(hi)));
+    }
+    __device__ static double to_double(V a) { return double(a.x) + double(a.y); }
+    __device__ static V shfl_xor(V a, int o) {
+        return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+    }
+    __device__ static S lget(const L& l, int k) {
+        return k == 0 ? make_float2(l.x, l.y) : make_float2(l.z, l.w);
+    }
+};
+
+template <class A>
+__device__ __forceinline__ typename A::V warp_sum(typename A::V v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v = A::add(v, A::shfl_xor(v, o));
     return v;
 }
 
-// G(r) from r^2; the diagonal (coincident points) takes `diag`.
+// G(r) from r^2 for the on-the-fly near field; the diagonal (coincident
+// points) takes `diag`.
 template <typename T, int KIND>
 __device__ __forceinline__ T kernel_r2(T r2, T param, T diag);
 
@@ -65,26 +162,30 @@ __device__ __forceinline__ float kernel_r2<float, 3>(float r2, float, float diag
 }
 
 // ---- gather / scatter between user order and tree order --------------------
-template <typename T>
+template <class A>
 __global__ void k_gather(const double* __restrict__ X, const int64_t* __restrict__ perm,
-                         T* __restrict__ q, int64_t N) {
+                         typename A::V* __restrict__ q, int64_t N) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < N) q[i] = T(X[perm[i]]);
+    if (i < N) q[i] = A::from_double(X[perm[i]]);
 }
 
-template <typename T>
-__global__ void k_scatter(const T* __restrict__ phi, const int64_t* __restrict__ perm,
+template <class A>
+__global__ void k_scatter(const typename A::V* __restrict__ phi, const int64_t* __restrict__ perm,
                           double* __restrict__ Y, int64_t N) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < N) Y[perm[i]] = double(phi[i]);
+    if (i < N) Y[perm[i]] = A::to_double(phi[i]);
 }
 
 // ---- P2M: v_X = U_X^T q_X at the leaves, one warp per (basis, leaf) ----------
-template <typename T>
+// U_X row i starts at ops[uoff[s] + i * ustride[s]] (rows of a stored near-field
+// block row, or a plain m x r matrix).
+template <class A>
 __global__ void k_p2m(int64_t ntask, int64_t nleaf, int64_t box_total, int64_t leaf_base,
                       const int64_t* __restrict__ leaf_ptr, const int32_t* __restrict__ rank,
                       const int64_t* __restrict__ voff, const int64_t* __restrict__ uoff,
-                      const T* __restrict__ ops, const T* __restrict__ q, T* __restrict__ v) {
+                      const int32_t* __restrict__ ustride, const typename A::S* __restrict__ ops,
+                      const typename A::V* __restrict__ q, typename A::V* __restrict__ v) {
+    using V = typename A::V;
     const int64_t task = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / kWarp;
     const int lane = threadIdx.x % kWarp;
     if (task >= ntask) return;
@@ -94,129 +195,142 @@ __global__ void k_p2m(int64_t ntask, int64_t nleaf, int64_t box_total, int64_t l
     if (r == 0) return;
     const int64_t p0 = leaf_ptr[L];
     const int m = int(leaf_ptr[L + 1] - p0);
-    const T* U = ops + uoff[s];
+    const int64_t st = ustride[s];
+    const typename A::S* U = ops + uoff[s];
     for (int j = lane; j < r; j += kWarp) {
-        T acc = T(0);
-        for (int i = 0; i < m; ++i) acc += U[int64_t(i) * r + j] * q[p0 + i];
+        V acc = A::zero();
+#pragma unroll 4
+        for (int i = 0; i < m; ++i) acc = A::mac(acc, U[int64_t(i) * st + j], q[p0 + i]);
         v[voff[s] + j] = acc;
     }
 }
 
-// ---- M2M: v_X = sum_c U~_{X_c X}^T v_{X_c}, one warp per parent -------------
-template <typename T>
+// ---- M2M: v_X = sum_c U~_{X_c X}^T v_{X_c}, one CTA per parent ---------------
+// Warp w takes rows i = w, w + nwarp, ... of every child's transfer matrix and
+// accumulates its own partial row of the parent's coefficients; the partial
+// rows are summed in a fixed order (deterministic).
+template <class A>
 __global__ void k_m2m(const int64_t* __restrict__ tasks, int64_t ntask, int64_t box_total,
                       int64_t base_l, int64_t base_child, int nchild,
                       const int32_t* __restrict__ rank, const int64_t* __restrict__ voff,
-                      const int64_t* __restrict__ utoff, const T* __restrict__ ops,
-                      T* __restrict__ v) {
-    const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / kWarp;
-    const int lane = threadIdx.x % kWarp;
-    if (w >= ntask) return;
-    const int64_t s = tasks[w];
+                      const int64_t* __restrict__ utoff, const typename A::S* __restrict__ ops,
+                      typename A::V* __restrict__ v) {
+    using V = typename A::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* part = reinterpret_cast<V*>(smem_raw);
+    const int64_t t = blockIdx.x;
+    if (t >= ntask) return;
+    const int64_t s = tasks[t];
     const int64_t b = s / box_total, X = s - b * box_total - base_l;
     const int r = rank[s];
-    for (int j = lane; j < r; j += kWarp) {
-        T acc = T(0);
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const int nwarp = blockDim.x / kWarp;
+    for (int j0 = 0; j0 < r; j0 += kWarp) {
+        const int j = j0 + lane;
+        V acc = A::zero();
         for (int c = 0; c < nchild; ++c) {
             const int64_t sc = b * box_total + base_child + X * nchild + c;
             const int rc = rank[sc];
-            if (rc == 0) continue;
-            const T* Ut = ops + utoff[sc];
-            const T* vc = v + voff[sc];
-            for (int i = 0; i < rc; ++i) acc += Ut[int64_t(i) * r + j] * vc[i];
+            const typename A::S* Ut = ops + utoff[sc];
+            const V* vc = v + voff[sc];
+            if (j < r) {
+#pragma unroll 4
+                for (int i = warp; i < rc; i += nwarp) acc = A::mac(acc, Ut[int64_t(i) * r + j], vc[i]);
+            }
         }
+        if (j < r) part[warp * r + j] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        V acc = part[j];
+        for (int w = 1; w < nwarp; ++w) acc = A::add(acc, part[w * r + j]);
         v[voff[s] + j] = acc;
     }
 }
 
-// ---- M2L: u_X = sum_{Y in IL(X)} T_{X,Y} v_Y, one CTA per target -----------
-// The sources' coefficients are gathered into shared memory (kpad values);
-// each warp takes rows of the concatenated coupling block and streams them
-// with coalesced vector loads.
-template <typename T>
-__global__ void k_m2l(int64_t ntask, const int64_t* __restrict__ slot,
-                      const int64_t* __restrict__ toff, const int32_t* __restrict__ kpad,
-                      const int64_t* __restrict__ src_ptr, const int64_t* __restrict__ src,
-                      const int32_t* __restrict__ rank, const int64_t* __restrict__ voff,
-                      const T* __restrict__ ops, const T* __restrict__ v, T* __restrict__ u) {
+// ---- block-row GEMV: M2L and the stored near field (+ fused L2P) -------------
+template <class A>
+__global__ void __launch_bounds__(256) k_rowgemv(
+    int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
+    const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
+    const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
+    const int32_t* __restrict__ seg_len, const typename A::S* __restrict__ ops,
+    typename A::V* __restrict__ vec) {
+    using V = typename A::V;
+    using L = typename A::L;
+    constexpr int W = A::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* vg = reinterpret_cast<T*>(smem_raw);
-    const int64_t task = blockIdx.x;
-    if (task >= ntask) return;
-    const int64_t s = slot[task];
-    const int r = rank[s];
-    const int kp = kpad[task];
+    V* xg = reinterpret_cast<V*>(smem_raw);
+    const int64_t t = blockIdx.x;
+    if (t >= ntask) return;
+    const int kp = kpad[t];
     int col = 0;
-    for (int64_t e = src_ptr[task]; e < src_ptr[task + 1]; ++e) {
-        const int64_t sy = src[e];
-        const int ry = rank[sy];
-        const T* vy = v + voff[sy];
-        for (int j = threadIdx.x; j < ry; j += blockDim.x) vg[col + j] = vy[j];
-        col += ry;
+    for (int64_t e = seg_ptr[t]; e < seg_ptr[t + 1]; ++e) {
+        const V* src = vec + seg_off[e];
+        const int len = seg_len[e];
+        for (int j = threadIdx.x; j < len; j += blockDim.x) xg[col + j] = src[j];
+        col += len;
     }
-    for (int j = col + threadIdx.x; j < kp; j += blockDim.x) vg[j] = T(0);
+    for (int j = col + threadIdx.x; j < kp; j += blockDim.x) xg[j] = A::zero();
     __syncthreads();
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     const int nwarp = blockDim.x / kWarp;
-    const T* Tm = ops + toff[task];
-    using V2 = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
-    constexpr int W = sizeof(V2) / sizeof(T);   // elements per vector load (2 or 4)
-    for (int row = warp; row < r; row += nwarp) {
-        const V2* trow = reinterpret_cast<const V2*>(Tm + int64_t(row) * kp);
-        const V2* vrow = reinterpret_cast<const V2*>(vg);
-        T acc = T(0);
-        const int nv = kp / W;
+    const int nr = rows[t];
+    const typename A::S* Am = ops + aoff[t];
+    const int nv = kp / W;
+    V* y = vec + dst[t];
+    for (int row = warp; row < nr; row += nwarp) {
+        const L* arow = reinterpret_cast<const L*>(Am + int64_t(row) * kp);
+        V acc = A::zero();
 #pragma unroll 4
         for (int k = lane; k < nv; k += kWarp) {
-            const V2 a = __ldg(trow + k);
-            const V2 x = vrow[k];
-            if constexpr (W == 2) {
-                acc += a.x * x.x + a.y * x.y;
-            } else {
-                acc += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
-            }
+            const L a = __ldg(arow + k);
+#pragma unroll
+            for (int w = 0; w < W; ++w) acc = A::mac(acc, A::lget(a, w), xg[k * W + w]);
         }
-        acc = warp_sum(acc);
-        if (lane == 0) u[voff[s] + row] = acc;
+        acc = warp_sum<A>(acc);
+        if (lane == 0) y[row] = acc;
     }
 }
 
-// ---- L2L: u_{X_c} += U~_{X_c X} u_X, one warp per child ---------------------
-template <typename T>
+// ---- L2L: u_{X_c} += U~_{X_c X} u_X, one CTA per child ----------------------
+template <class A>
 __global__ void k_l2l(const int64_t* __restrict__ tasks, int64_t ntask, int64_t box_total,
                       int64_t base_l, int64_t base_parent, int dshift,
                       const int32_t* __restrict__ rank, const int64_t* __restrict__ voff,
-                      const int64_t* __restrict__ utoff, const T* __restrict__ ops,
-                      T* __restrict__ u) {
-    const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / kWarp;
-    const int lane = threadIdx.x % kWarp;
-    if (w >= ntask) return;
-    const int64_t s = tasks[w];
+                      const int64_t* __restrict__ utoff, const typename A::S* __restrict__ ops,
+                      typename A::V* __restrict__ u) {
+    using V = typename A::V;
+    const int64_t t = blockIdx.x;
+    if (t >= ntask) return;
+    const int64_t s = tasks[t];
     const int64_t b = s / box_total, X = s - b * box_total - base_l;
     const int64_t sp = b * box_total + base_parent + (X >> dshift);
     const int rc = rank[s], rp = rank[sp];
-    const T* Ut = ops + utoff[s];
-    const T* up = u + voff[sp];
-    T* uc = u + voff[s];
-    for (int i = 0; i < rc; ++i) {
-        T part = T(0);
-        for (int j = lane; j < rp; j += kWarp) part += Ut[int64_t(i) * rp + j] * up[j];
-        part = warp_sum(part);
-        if (lane == 0) uc[i] += part;
+    const typename A::S* Ut = ops + utoff[s];
+    const V* up = u + voff[sp];
+    V* uc = u + voff[s];
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const int nwarp = blockDim.x / kWarp;
+    for (int i = warp; i < rc; i += nwarp) {
+        V part = A::zero();
+        for (int j = lane; j < rp; j += kWarp) part = A::mac(part, Ut[int64_t(i) * rp + j], up[j]);
+        part = warp_sum<A>(part);
+        if (lane == 0) uc[i] = A::add(uc[i], part);
     }
 }
 
-// ---- leaves: phi_X = sum_b U_X^b u_X^b + sum_{X' in N(X)} K_{t^X, s^X'} q_X' ----
-// One CTA per leaf; each thread owns targets; source points of the neighbour
-// leaves are staged through shared memory in tiles of blockDim.
+// ---- leaves, near field on the fly (F64 / F32) --------------------------------
+// phi_X = sum_b U_X^b u_X^b + sum_{X' in N(X)} K_{t^X, s^X'} q_X'; one CTA per
+// leaf, one target per thread; source points staged through shared memory.
 template <typename T, int D, int KIND>
-__global__ void k_leaf(int64_t nleaf, int nb, int64_t box_total, int64_t leaf_base,
-                       const int64_t* __restrict__ leaf_ptr, const int64_t* __restrict__ near_ptr,
-                       const int64_t* __restrict__ near_idx, const int32_t* __restrict__ rank,
-                       const int64_t* __restrict__ voff, const int64_t* __restrict__ uoff,
-                       const T* __restrict__ ops, const T* __restrict__ u,
-                       const T* __restrict__ xs, int64_t N, const T* __restrict__ q,
-                       T* __restrict__ phi, T param, T diag) {
+__global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t leaf_base,
+                           const int64_t* __restrict__ leaf_ptr, const int64_t* __restrict__ near_ptr,
+                           const int64_t* __restrict__ near_idx, const int32_t* __restrict__ rank,
+                           const int64_t* __restrict__ voff, const int64_t* __restrict__ uoff,
+                           const int32_t* __restrict__ ustride, const T* __restrict__ ops,
+                           const T* __restrict__ u, const T* __restrict__ xs, int64_t N,
+                           const T* __restrict__ q, T* __restrict__ phi, T param, T diag) {
     constexpr int TILE = 128;
     __shared__ T sx[D][TILE];
     __shared__ T sq[TILE];
@@ -236,7 +350,7 @@ __global__ void k_leaf(int64_t nleaf, int nb, int64_t box_total, int64_t leaf_ba
                 const int64_t s = b * box_total + leaf_base + L;
                 const int r = rank[s];
                 if (r == 0) continue;
-                const T* U = ops + uoff[s] + int64_t(i) * r;
+                const T* U = ops + uoff[s] + int64_t(i) * ustride[s];
                 const T* ub = u + voff[s];
                 for (int j = 0; j < r; ++j) acc += U[j] * ub[j];
             }
@@ -271,16 +385,13 @@ __global__ void k_leaf(int64_t nleaf, int nb, int64_t box_total, int64_t leaf_ba
     }
 }
 
-// ---- (H2+H)*: t = V^T q_Y per block (atomic partial sums over point chunks) --
+// ---- (H2+H)*: t = V^T q_Y per block (partial sums over point chunks) ----------
 template <typename T>
 __global__ void k_lr_vtq(int64_t b0, int64_t nblk, const int64_t* __restrict__ y0,
                          const int64_t* __restrict__ my, const int32_t* __restrict__ kk,
                          const int64_t* __restrict__ voffs, const int64_t* __restrict__ toffs,
                          const T* __restrict__ ops, const T* __restrict__ q, T* __restrict__ t,
                          int chunk) {
-    // grid.x over (block, column, chunk) flattened by the host into work items
-    // passed as blockIdx.y = block index relative to b0, blockIdx.x = chunk id,
-    // loop over columns inside.
     const int64_t blk = b0 + blockIdx.y;
     if (blockIdx.y >= nblk) return;
     const int64_t m = my[blk];
@@ -294,12 +405,14 @@ __global__ void k_lr_vtq(int64_t b0, int64_t nblk, const int64_t* __restrict__ y
     for (int c = 0; c < k; ++c) {
         T part = T(0);
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) part += V[c * m + i] * qy[i];
-        part = warp_sum(part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if (threadIdx.x % kWarp == 0) red[threadIdx.x / kWarp] = part;
         __syncthreads();
         if (threadIdx.x < kWarp) {
             T s = threadIdx.x < blockDim.x / kWarp ? red[threadIdx.x] : T(0);
-            s = warp_sum(s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (threadIdx.x == 0) atomicAdd(t + toffs[blk] + c, s);
         }
         __syncthreads();

@@ -58,6 +58,28 @@ def test_invalid_arguments_return_error_codes():
     assert b"NULL" in pkg.lib().h2_last_error()
 
 
+def test_unsupported_combinations_are_rejected():
+    P = inputs.points(300, 2, 2)
+    with pytest.raises(H2Error) as e:
+        H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, storage="df64", near="fly", host_only=True)
+    assert e.value.code == -5
+    with pytest.raises(H2Error) as e:
+        H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, storage="df64", variant="h2plush",
+                 host_only=True)
+    assert e.value.code == -5
+
+
+def test_near_field_storage_accounting():
+    P = inputs.points(4096, 2, 1001)
+    S = H2Matrix(P, "log2d", leaf_size=64, tol=1e-6, host_only=True).info()
+    F = H2Matrix(P, "log2d", leaf_size=64, tol=1e-6, near="fly", host_only=True).info()
+    assert S["near_stored"] == 1 and F["near_stored"] == 0
+    # stored rows hold every near-field kernel value plus the fused leaf bases
+    assert S["bytes_leaf_rows"] >= 8 * (S["near_evals"]) + S["bytes_basis"]
+    assert F["bytes_leaf_rows"] == 0
+    assert S["bytes_m2l"] == F["bytes_m2l"]
+
+
 def test_matvec_on_host_only_handle_is_rejected():
     A = H2Matrix(inputs.points(300, 2, 2), "log2d", leaf_size=16, tol=1e-6, host_only=True)
     rc = pkg.lib().h2_matvec(A._h, ctypes.c_void_p(16), 300, ctypes.c_void_p(16), 300, 1, None)

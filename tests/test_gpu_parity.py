@@ -9,8 +9,11 @@ Two bars, both on identical seeded inputs:
   up to ~1/eps) and the sums run in a different order.  Measured: ~1e-12 of
   max|phi| in fp64 (the oracle's two operator formulas already differ by that
   much), so the fp64 bar is 1e-10 * max|phi|.  In fp32 storage every operator
-  entry and kernel value carries ~6e-8 relative rounding; the bar is
-  2e-5 * max|phi| (and 1e-5 in the 2-norm).
+  entry and kernel value carries a relative rounding u = 2^-24, and the error
+  of row i scales with the absolute sum (|K| |q|)_i, not with |phi_i| (log r
+  and 1/r sums cancel by a factor ~20): it passes through the chain
+  L2P L2L^k M2L M2M^k P2M whose ACA skeletons amplify by O(10).  The fp32 bar
+  is |y_i - ref_i| <= 64 u (|K| |q|)_i (measured worst: ~45 u for 2D log r).
 * against the plain definition phi = K q: relative 2-norm error <= 10 eps,
   full dense for N <= 32k and 1024 sampled exact rows above.  Where the
   method itself (the oracle's K~ on the same input) already exceeds 10 eps,
@@ -30,7 +33,20 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 F64_TOL = 1e-10
-F32_TOL = 2e-5
+# (storage, near-field mode): fp64 / double-float with stored near-field blocks
+# or fp64 on the fly; fp32 on the fly or stored.  Double-float keeps 48 bits of
+# every entry, so it meets the fp64 bar.
+MODES = [("f64", None), ("f64", "fly"), ("df64", None), ("f32", None), ("f32", "stored")]
+
+
+def _check_mode(y, ref, storage, kind, P, q):
+    if storage != "f32":
+        assert _maxrel(y, ref) <= F64_TOL
+        return
+    bound = 64 * 2.0 ** -24 * (np.abs(dense.matrix(kind, P)) @ np.abs(q))
+    worst = float((np.abs(y - ref) / bound).max())
+    print(f"fp32 {kind}: max |y - ref| / (64 u |K||q|) = {worst:.3f}")
+    assert worst <= 1.0
 
 
 def _dev(a):
@@ -63,6 +79,22 @@ def test_c1_2d_log_n4096_matches_oracle_and_dense(variant):
     ref = h2.H2(P, "log2d", variant=variant, n_max=64, eps=1e-8).matvec(q)
     assert _maxrel(y, ref) <= F64_TOL
     _dense_bar(y, ref, dense.product("log2d", P, q), 1e-8)
+
+
+@pytest.mark.parametrize("storage,near", MODES)
+def test_storage_and_near_modes_match_oracle(storage, near):
+    """Every storage precision and near-field mode on 2D log r and 3D 1/r.
+    fp32 storage is meant for tolerances >= 1e-6 (or as the inner product of an
+    iterative refinement): at eps = 1e-8 in 2D its rounding alone reaches ~7e-5
+    of max|phi| (measured), so it is checked at eps = 1e-6."""
+    eps2 = 1e-6 if storage == "f32" else 1e-8
+    for kind, d, N, n_max, eps in [("log2d", 2, 4096, 64, eps2), ("invr", 3, 7000, 32, 1e-6)]:
+        P = inputs.points(N, d, 1001 + d)
+        q = inputs.rhs(N, 1, 2001 + d)
+        A = H2Matrix(P, kind, leaf_size=n_max, tol=eps, storage=storage, near=near)
+        y = _gpu_mvp(A, q)
+        ref = h2.H2(P, kind, n_max=n_max, eps=eps).matvec(q)
+        _check_mode(y, ref, storage, kind, P, q)
 
 
 @pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt"])
@@ -107,7 +139,7 @@ def test_f32_storage_against_oracle():
     A = H2Matrix(P, "invr", leaf_size=32, tol=1e-6, storage="f32")
     y = _gpu_mvp(A, q)
     ref = h2.H2(P, "invr", n_max=32, eps=1e-6).matvec(q)
-    assert _maxrel(y, ref) <= F32_TOL
+    _check_mode(y, ref, "f32", "invr", P, q)
     assert dense.relative_error(y, ref) <= 1e-5
     _dense_bar(y, ref, dense.product("invr", P, q), 1e-6)
 
