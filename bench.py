@@ -257,6 +257,7 @@ def bench_ours(args, rank, world):
                    "l2": "operators larger than L2 (no flush)",
                    "build_seconds": round(build_s, 2),
                    "device_bytes": info["bytes_device"],
+                   "autotuned_rows_per_warp": {"m2l": info["rw_m2l"], "leaf": info["rw_leaf"]},
                    "ranks": info["ranks"]},
         "clocks": clk,
         "e2e": {"value": world * N * nrhs / (e2e_ms / 1e3), "unit": UNIT,

@@ -146,6 +146,7 @@ typedef struct {
                                       the near field is evaluated on the fly)               */
     int64_t leaf_src_coeffs;       /* leaf block rows: coefficients gathered, summed        */
     int     near_stored;           /* 1: near field from stored blocks, 0: on the fly      */
+    int     rw_m2l, rw_leaf;       /* rows per warp the build-time autotuner chose          */
     int64_t bytes_lowrank;         /* stored (H2+H)* U, V factors                          */
     int64_t bytes_device;          /* total device bytes held by the handle                */
     int64_t alg_bytes_per_rhs;     /* algorithmic HBM bytes of one MVP with one RHS      */

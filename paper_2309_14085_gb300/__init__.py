@@ -49,7 +49,7 @@ class Stats(ctypes.Structure):
                 ("bytes_m2l", ctypes.c_int64), ("m2l_src_coeffs", ctypes.c_int64),
                 ("m2l_dst_coeffs", ctypes.c_int64), ("vlen", ctypes.c_int64),
                 ("bytes_leaf_rows", ctypes.c_int64), ("leaf_src_coeffs", ctypes.c_int64),
-                ("near_stored", ctypes.c_int),
+                ("near_stored", ctypes.c_int), ("rw_m2l", ctypes.c_int), ("rw_leaf", ctypes.c_int),
                 ("bytes_lowrank", ctypes.c_int64),
                 ("bytes_device", ctypes.c_int64), ("alg_bytes_per_rhs", ctypes.c_int64),
                 ("build_seconds", ctypes.c_double)]

@@ -41,8 +41,9 @@ enum Stage { ST_GATHER, ST_P2M, ST_M2M, ST_M2L, ST_L2L, ST_LEAF, ST_LOWRANK, ST_
 struct DevRowTasks {
     int64_t n = 0;
     size_t smem = 0;
+    int rw = 4;                   // rows per warp (autotuned for the large lists)
     int64_t *dst = nullptr, *aoff = nullptr, *seg_ptr = nullptr, *seg_off = nullptr;
-    int32_t *rows = nullptr, *kpad = nullptr, *seg_len = nullptr;
+    int32_t *rows = nullptr, *kpad = nullptr, *seg_len = nullptr, *seg_col = nullptr;
 };
 
 struct h2_handle_s {
@@ -65,11 +66,10 @@ struct h2_handle_s {
     int64_t* uoff = nullptr;
     int32_t* ustride = nullptr;
     int64_t* utoff = nullptr;
-    int64_t* m2m_tasks = nullptr;  // all levels concatenated
-    int64_t* l2l_tasks = nullptr;
-    std::vector<int64_t> m2m_lptr, l2l_lptr;   // host offsets per level
-    size_t m2m_smem = 0;
-    DevRowTasks m2l, leaf;
+    DevRowTasks p2m, m2l, leaf;
+    std::vector<DevRowTasks> m2m;              // per parent level
+    std::vector<DevRowTasks> l2l;              // per child level
+    double tune_ms[2][3] = {};                 // autotuner timings (m2l, leaf) x rw 2/4/8
     // (H2+H)*
     int64_t *lr_y0 = nullptr, *lr_my = nullptr, *lr_uoff = nullptr, *lr_voff = nullptr,
             *lr_toff = nullptr, *lr_x0 = nullptr, *lr_mx = nullptr, *lr_gptr = nullptr;
@@ -142,7 +142,59 @@ int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize
     H2_TRY(dev_upload(h, &D.rows, R.rows));
     H2_TRY(dev_upload(h, &D.kpad, R.kpad));
     H2_TRY(dev_upload(h, &D.seg_len, R.seg_len));
-    D.smem = size_t(R.kpad_max) * vsize;
+    H2_TRY(dev_upload(h, &D.seg_col, R.seg_col));
+    D.smem = 0;
+    (void)vsize;
+    return H2_OK;
+}
+
+template <class A, int RW>
+void launch_rows_rw(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate) {
+    h2::k_rowgemv<A, RW><<<unsigned(R.n), 256, 0, s>>>(
+        R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
+        static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate);
+}
+
+template <class A>
+void launch_rows(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate) {
+    if (R.n == 0) return;
+    if (R.rw == 2) launch_rows_rw<A, 2>(R, ops, vec, s, accumulate);
+    else if (R.rw == 8) launch_rows_rw<A, 8>(R, ops, vec, s, accumulate);
+    else launch_rows_rw<A, 4>(R, ops, vec, s, accumulate);
+}
+
+// Autotuner: for the two large block-row lists (M2L and the stored leaf rows)
+// time 2, 4 and 8 rows per warp on the device (the coefficient buffer is
+// scratch here) and keep the fastest.  Small lists use 4.
+template <class A>
+int autotune(h2_handle h) {
+    cudaEvent_t e0, e1;
+    H2_CUDA(cudaEventCreate(&e0));
+    H2_CUDA(cudaEventCreate(&e1));
+    DevRowTasks* lists[2] = {&h->m2l, &h->leaf};
+    const int rws[3] = {2, 4, 8};
+    for (int li = 0; li < 2; ++li) {
+        DevRowTasks& R = *lists[li];
+        if (R.n == 0) continue;
+        double best = 1e30;
+        int best_rw = 4;
+        for (int k = 0; k < 3; ++k) {
+            R.rw = rws[k];
+            launch_rows<A>(R, h->ops, h->vec, 0, 0);          // warm-up
+            H2_CUDA(cudaEventRecord(e0, 0));
+            for (int it = 0; it < 3; ++it) launch_rows<A>(R, h->ops, h->vec, 0, 0);
+            H2_CUDA(cudaEventRecord(e1, 0));
+            H2_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            h->tune_ms[li][k] = ms / 3.0;
+            if (ms < best) { best = ms; best_rw = rws[k]; }
+        }
+        R.rw = best_rw;
+    }
+    H2_CUDA(cudaEventDestroy(e0));
+    H2_CUDA(cudaEventDestroy(e1));
+    H2_CUDA(cudaGetLastError());
     return H2_OK;
 }
 
@@ -193,30 +245,15 @@ int upload(h2_handle h) {
     H2_TRY(dev_upload(h, &h->uoff, P.uoff));
     H2_TRY(dev_upload(h, &h->ustride, P.ustride));
     H2_TRY(dev_upload(h, &h->utoff, P.utoff));
-    std::vector<int64_t> m2m, l2l;
-    h->m2m_lptr.assign(t.kappa + 2, 0);
-    h->l2l_lptr.assign(t.kappa + 2, 0);
-    for (int l = 0; l <= t.kappa; ++l) {
-        m2m.insert(m2m.end(), P.m2m_tasks[l].begin(), P.m2m_tasks[l].end());
-        l2l.insert(l2l.end(), P.l2l_tasks[l].begin(), P.l2l_tasks[l].end());
-        h->m2m_lptr[l + 1] = int64_t(m2m.size());
-        h->l2l_lptr[l + 1] = int64_t(l2l.size());
-    }
-    H2_TRY(dev_upload(h, &h->m2m_tasks, m2m));
-    H2_TRY(dev_upload(h, &h->l2l_tasks, l2l));
-    h->m2m_smem = size_t(8) * std::max(P.rank_max, 1) * sizeof(V);
+    H2_TRY(upload_rows(h, h->p2m, P.p2m, sizeof(V)));
     H2_TRY(upload_rows(h, h->m2l, P.m2l, sizeof(V)));
     H2_TRY(upload_rows(h, h->leaf, P.leaf, sizeof(V)));
-    const size_t smem_cap = 227 * 1024;
-    const size_t rows_smem = std::max(h->m2l.smem, h->leaf.smem);
-    if (rows_smem > smem_cap || h->m2m_smem > smem_cap)
-        return fail(H2_E_UNSUPPORTED, "coefficients of one block row exceed shared memory (ranks too high)");
-    if (rows_smem > 48 * 1024)
-        H2_CUDA(cudaFuncSetAttribute(h2::k_rowgemv<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(rows_smem)));
-    if (h->m2m_smem > 48 * 1024)
-        H2_CUDA(cudaFuncSetAttribute(h2::k_m2m<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(h->m2m_smem)));
+    h->m2m.assign(t.kappa + 1, DevRowTasks());
+    h->l2l.assign(t.kappa + 1, DevRowTasks());
+    for (int l = 0; l <= t.kappa; ++l) {
+        H2_TRY(upload_rows(h, h->m2m[l], P.m2m[l], sizeof(V)));
+        H2_TRY(upload_rows(h, h->l2l[l], P.l2l[l], sizeof(V)));
+    }
     // (H2+H)* groups: consecutive blocks of one level with the same target box
     const int64_t nblk = int64_t(P.lr_k.size());
     h->lr_gptr_host.clear();
@@ -242,6 +279,7 @@ int upload(h2_handle h) {
     H2_TRY(dev_upload(h, &h->lr_voff, P.lr_voff));
     H2_TRY(dev_upload(h, &h->lr_toff, P.lr_toff));
     H2_CUDA(cudaDeviceSynchronize());
+    H2_TRY(autotune<A>(h));
     return H2_OK;
 }
 
@@ -271,13 +309,6 @@ void launch_leaf_d(h2_handle h, cudaStream_t s) {
     }
 }
 
-template <class A>
-void launch_rows(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s) {
-    if (R.n == 0) return;
-    h2::k_rowgemv<A><<<unsigned(R.n), 256, R.smem, s>>>(
-        R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len,
-        static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec));
-}
 
 void mark(h2_handle h, cudaStream_t s, int stage) {
     if (h->profile) cudaEventRecord(h->ev[stage], s);
@@ -337,36 +368,27 @@ int matvec_one(h2_handle h, const double* X, double* Y, cudaStream_t s) {
     ++nl;
     h2::k_gather<A><<<nblocks(t.N, 256), 256, 0, s>>>(X, h->perm, q, t.N);
     mark(h, s, ST_P2M);
-    if (P.nb > 0 && P.vlen > 0) {
-        const int64_t ntask = P.nb * nleaf;
+    if (h->p2m.n > 0) {
         ++nl;
-        h2::k_p2m<A><<<nblocks(ntask * 32, 256), 256, 0, s>>>(
-            ntask, nleaf, P.box_total, P.box_base[K], h->leaf_ptr, h->rank, h->voff, h->uoff,
-            h->ustride, ops, q, v);
+        launch_rows<A>(h->p2m, ops, vec, s, 0);
     }
     mark(h, s, ST_M2M);
     for (int l = K - 1; l >= 1; --l) {
-        const int64_t n = h->m2m_lptr[l + 1] - h->m2m_lptr[l];
-        if (n == 0) continue;
+        if (h->m2m[l].n == 0) continue;
         ++nl;
-        h2::k_m2m<A><<<unsigned(n), 256, h->m2m_smem, s>>>(
-            h->m2m_tasks + h->m2m_lptr[l], n, P.box_total, P.box_base[l], P.box_base[l + 1], 1 << d,
-            h->rank, h->voff, h->utoff, ops, v);
+        launch_rows<A>(h->m2m[l], ops, vec, s, 0);
     }
     mark(h, s, ST_M2L);
     if (P.vlen > 0) cudaMemsetAsync(u, 0, sizeof(V) * P.vlen, s);
     if (h->m2l.n > 0) {
         ++nl;
-        launch_rows<A>(h->m2l, ops, vec, s);
+        launch_rows<A>(h->m2l, ops, vec, s, 0);
     }
     mark(h, s, ST_L2L);
     for (int l = 2; l <= K; ++l) {
-        const int64_t n = h->l2l_lptr[l + 1] - h->l2l_lptr[l];
-        if (n == 0) continue;
+        if (h->l2l[l].n == 0) continue;
         ++nl;
-        h2::k_l2l<A><<<unsigned(n), 128, 0, s>>>(
-            h->l2l_tasks + h->l2l_lptr[l], n, P.box_total, P.box_base[l], P.box_base[l - 1], d,
-            h->rank, h->voff, h->utoff, ops, u);
+        launch_rows<A>(h->l2l[l], ops, vec, s, 1);
     }
     mark(h, s, ST_LEAF);
     if (P.near_stored) {
@@ -374,7 +396,7 @@ int matvec_one(h2_handle h, const double* X, double* Y, cudaStream_t s) {
         cudaMemsetAsync(phi, 0, sizeof(V) * t.N, s);
         if (h->leaf.n > 0) {
             ++nl;
-            launch_rows<A>(h->leaf, ops, vec, s);
+            launch_rows<A>(h->leaf, ops, vec, s, 0);
         }
     } else if constexpr (!std::is_same<A, h2::DF>::value) {
         using T = typename A::V;
@@ -585,6 +607,8 @@ int h2_info(h2_handle h, h2_stats* st) {
     st->bytes_leaf_rows = P.leaf.entries * ts;
     st->leaf_src_coeffs = P.leaf.src_coeffs;
     st->near_stored = P.near_stored;
+    st->rw_m2l = h->m2l.rw;
+    st->rw_leaf = h->leaf.rw;
     st->vlen = P.vlen;
     st->bytes_lowrank = nlr * ts;
     st->near_pairs = H.near_pairs;

@@ -620,27 +620,63 @@ void pack(Host& H) {
             }
         }
     }
+    // L2L matrices U~_{X_c X}: r_c x pad4(r_X) row-major, one L2L task per child
+    // with both ranks > 0
+    P.l2l.assign(K + 1, RowTasks());
     for (int b = 0; b < P.nb; ++b) {
         const Basis& B = H.bases[b];
         for (int l = B.lmin + 1; l <= K; ++l)
             for (int64_t X = 0; X < t.nboxes(l); ++X) {
-                const int64_t o = place(int64_t(B.Ut[l][X].size()));
+                const int rc = B.rank(l, X), rp = B.rank(l - 1, X >> d);
+                const int64_t kp = pad4(rp);
+                const int64_t o = place(int64_t(rc) * kp);
                 P.utoff[slot(b, l, X)] = o;
-                copies.push_back({&B.Ut[l][X], o, 1, int64_t(B.Ut[l][X].size()),
-                                  int64_t(B.Ut[l][X].size())});
+                copies.push_back({&B.Ut[l][X], o, rc, rp, kp});
+                if (rc > 0 && rp > 0) {
+                    const int64_t sp = slot(b, l - 1, X >> d);
+                    P.l2l[l].add(P.u_base + P.voff[slot(b, l, X)], rc, int32_t(kp), o);
+                    P.l2l[l].seg(P.u_base + P.voff[sp], rp);
+                    P.l2l[l].close();
+                }
             }
     }
-    P.m2m_tasks.assign(K + 1, {});
-    P.l2l_tasks.assign(K + 1, {});
+    // P2M and M2M as block rows over transposed copies: v_X = U_X^T q_X at the
+    // leaves (r x pad4(m)), v_X = [U~_{X_1 X}^T | ... | U~_{X_2^d X}^T] [v_1; ...]
+    // above (r_X x pad4(sum_c r_c)); filled after the allocation.
+    struct TBlock { int b, l; int64_t X, o, kp; };
+    std::vector<TBlock> tblocks;
+    P.p2m = RowTasks();
+    P.m2m.assign(K + 1, RowTasks());
     for (int b = 0; b < P.nb; ++b) {
         const Basis& B = H.bases[b];
+        if (K < B.lmin) continue;
+        for (int64_t X = 0; X < nleaf; ++X) {
+            const int r = B.rank(K, X);
+            const int64_t m = t.leaf_ptr[X + 1] - t.leaf_ptr[X];
+            if (r == 0 || m == 0) continue;
+            const int64_t kp = pad4(m);
+            const int64_t o = place(int64_t(r) * kp);
+            tblocks.push_back({b, K, X, o, kp});
+            P.p2m.add(P.v_base + P.voff[slot(b, K, X)], r, int32_t(kp), o);
+            P.p2m.seg(P.q_base + t.leaf_ptr[X], int32_t(m));
+            P.p2m.close();
+        }
         for (int l = B.lmin; l < K; ++l)
-            for (int64_t X = 0; X < t.nboxes(l); ++X)
-                if (B.rank(l, X) > 0) P.m2m_tasks[l].push_back(slot(b, l, X));
-        for (int l = B.lmin + 1; l <= K; ++l)
-            for (int64_t X = 0; X < t.nboxes(l); ++X)
-                if (B.rank(l, X) > 0 && B.rank(l - 1, X >> d) > 0)
-                    P.l2l_tasks[l].push_back(slot(b, l, X));
+            for (int64_t X = 0; X < t.nboxes(l); ++X) {
+                const int r = B.rank(l, X);
+                int64_t kc = 0;
+                for (int c = 0; c < (1 << d); ++c) kc += B.rank(l + 1, X * (int64_t(1) << d) + c);
+                if (r == 0 || kc == 0) continue;
+                const int64_t kp = pad4(kc);
+                const int64_t o = place(int64_t(r) * kp);
+                tblocks.push_back({b, l, X, o, kp});
+                P.m2m[l].add(P.v_base + P.voff[slot(b, l, X)], r, int32_t(kp), o);
+                for (int c = 0; c < (1 << d); ++c) {
+                    const int64_t sc = slot(b, l + 1, X * (int64_t(1) << d) + c);
+                    if (P.rank[sc] > 0) P.m2m[l].seg(P.v_base + P.voff[sc], P.rank[sc]);
+                }
+                P.m2m[l].close();
+            }
     }
     // M2L: one block row per target, rows padded with zeros to a multiple of 4
     P.m2l = RowTasks();
@@ -705,6 +741,28 @@ void pack(Host& H) {
         double* dst = P.ops.data() + C.dst;
         for (int64_t r = 0; r < C.rows; ++r)
             std::memcpy(dst + r * C.pad, src + r * C.cols, size_t(C.cols) * sizeof(double));
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < int64_t(tblocks.size()); ++k) {
+        const TBlock& T = tblocks[k];
+        const Basis& B = H.bases[T.b];
+        double* A = P.ops.data() + T.o;
+        const int r = B.rank(T.l, T.X);
+        if (T.l == K) {                      // U_X^T: A[j][i] = U_X[i][j]
+            const int64_t m = t.leaf_ptr[T.X + 1] - t.leaf_ptr[T.X];
+            for (int64_t i = 0; i < m; ++i)
+                for (int j = 0; j < r; ++j) A[j * T.kp + i] = B.U[T.X][i * r + j];
+        } else {                             // U~_c^T blocks side by side
+            int64_t col = 0;
+            for (int c = 0; c < (1 << d); ++c) {
+                const int64_t Xc = T.X * (int64_t(1) << d) + c;
+                const int rc = B.rank(T.l + 1, Xc);
+                const std::vector<double>& Ut = B.Ut[T.l + 1][Xc];   // rc x r
+                for (int i = 0; i < rc; ++i)
+                    for (int j = 0; j < r; ++j) A[j * T.kp + col + i] = Ut[size_t(i) * r + j];
+                col += rc;
+            }
+        }
     }
     if (P.near_stored) {
 #pragma omp parallel for schedule(dynamic, 8)

@@ -87,19 +87,24 @@ struct LowRankBlock {
 // with x the concatenation of the segments (off, len) of the coefficient buffer.
 struct RowTasks {
     std::vector<int64_t> dst, aoff, seg_ptr{0}, seg_off;
-    std::vector<int32_t> rows, kpad, seg_len;
+    std::vector<int32_t> rows, kpad, seg_len, seg_col;
+    int32_t cur_col = 0;
     int32_t kpad_max = 0;
     int64_t entries = 0;       // sum of rows * kpad
     int64_t src_coeffs = 0;    // sum of kpad (coefficients gathered)
     int64_t dst_coeffs = 0;    // sum of rows
     void add(int64_t d, int32_t r, int32_t kp, int64_t a) {
         dst.push_back(d); rows.push_back(r); kpad.push_back(kp); aoff.push_back(a);
+        cur_col = 0;
         kpad_max = std::max(kpad_max, kp);
         entries += int64_t(r) * kp;
         src_coeffs += kp;
         dst_coeffs += r;
     }
-    void seg(int64_t off, int32_t len) { seg_off.push_back(off); seg_len.push_back(len); }
+    void seg(int64_t off, int32_t len) {
+        seg_off.push_back(off); seg_len.push_back(len); seg_col.push_back(cur_col);
+        cur_col += len;
+    }
     void close() { seg_ptr.push_back(int64_t(seg_off.size())); }
     int64_t size() const { return int64_t(dst.size()); }
 };
@@ -119,7 +124,9 @@ struct Packed {
     std::vector<int64_t> uoff;        // [slot] leaf basis U row 0 (leaf slots)
     std::vector<int32_t> ustride;     // [slot] distance between rows of U
     std::vector<int64_t> utoff;       // [slot] L2L matrix (child slot), -1 if none
-    std::vector<std::vector<int64_t>> m2m_tasks, l2l_tasks;   // [level]
+    RowTasks p2m;                     // v_X = U_X^T q_X (transposed copies of the leaf bases)
+    std::vector<RowTasks> m2m;        // [parent level] v_X = [U~_c1^T | U~_c2^T | ...] v
+    std::vector<RowTasks> l2l;        // [child level] u_c += U~_c u_parent
     RowTasks m2l, leaf;               // M2L targets; stored near field + L2P
     int32_t rank_max = 0;
     int64_t near_entries = 0;         // stored near-field kernel values

@@ -20,14 +20,17 @@
 //         multipole / local coefficients of every (basis, level, box) slot.
 //   xs    coordinates in tree order, structure of arrays (xs[k * N + i]).
 //
-// A "block row" task computes y[dst + i] = sum_k A[i * kpad + k] x[k] for
+// A "block row" task computes y[dst + i] (+)= sum_k A[i * kpad + k] x[k] for
 // i < rows, where x is the concatenation of segments of `vec` (gathered into
 // shared memory) and A is stored row-major, zero padded to kpad (a multiple of
-// 4 entries, so rows start 16-byte aligned).  M2L is one task per target
-// cluster (x = the sources' multipoles, y = its local coefficients); the
-// stored near field is one task per leaf with the leaf's bases appended as
-// extra columns (x = neighbours' charges then the leaf's local coefficients),
-// so L2P is fused into it.
+// 4 entries, so rows start 16-byte aligned).  Every step of the MVP except the
+// on-the-fly near field is a list of such tasks:
+//   P2M  one task per (basis, leaf): A = U_X^T, x = q_X, y = v_X;
+//   M2M  one per parent: A = [U~_{X_1 X}^T | ...], x = the children's v, y = v_X;
+//   M2L  one per target: A = [T_{X,Y_1} | ...], x = the sources' v, y = u_X;
+//   L2L  one per child: A = U~_{X_c X}, x = u_X, y = u_{X_c} (accumulate);
+//   leaf one per leaf: A = [K_{t^X, s^X'} ... | U_X^far | U_X^ver],
+//        x = the neighbours' q then the leaf's u, y = phi_X (L2P fused).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -176,147 +179,83 @@ __global__ void k_scatter(const typename A::V* __restrict__ phi, const int64_t* 
     if (i < N) Y[perm[i]] = A::to_double(phi[i]);
 }
 
-// ---- P2M: v_X = U_X^T q_X at the leaves, one warp per (basis, leaf) ----------
-// U_X row i starts at ops[uoff[s] + i * ustride[s]] (rows of a stored near-field
-// block row, or a plain m x r matrix).
-template <class A>
-__global__ void k_p2m(int64_t ntask, int64_t nleaf, int64_t box_total, int64_t leaf_base,
-                      const int64_t* __restrict__ leaf_ptr, const int32_t* __restrict__ rank,
-                      const int64_t* __restrict__ voff, const int64_t* __restrict__ uoff,
-                      const int32_t* __restrict__ ustride, const typename A::S* __restrict__ ops,
-                      const typename A::V* __restrict__ q, typename A::V* __restrict__ v) {
-    using V = typename A::V;
-    const int64_t task = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / kWarp;
-    const int lane = threadIdx.x % kWarp;
-    if (task >= ntask) return;
-    const int64_t b = task / nleaf, L = task - b * nleaf;
-    const int64_t s = b * box_total + leaf_base + L;
-    const int r = rank[s];
-    if (r == 0) return;
-    const int64_t p0 = leaf_ptr[L];
-    const int m = int(leaf_ptr[L + 1] - p0);
-    const int64_t st = ustride[s];
-    const typename A::S* U = ops + uoff[s];
-    for (int j = lane; j < r; j += kWarp) {
-        V acc = A::zero();
-#pragma unroll 4
-        for (int i = 0; i < m; ++i) acc = A::mac(acc, U[int64_t(i) * st + j], q[p0 + i]);
-        v[voff[s] + j] = acc;
-    }
-}
-
-// ---- M2M: v_X = sum_c U~_{X_c X}^T v_{X_c}, one CTA per parent ---------------
-// Warp w takes rows i = w, w + nwarp, ... of every child's transfer matrix and
-// accumulates its own partial row of the parent's coefficients; the partial
-// rows are summed in a fixed order (deterministic).
-template <class A>
-__global__ void k_m2m(const int64_t* __restrict__ tasks, int64_t ntask, int64_t box_total,
-                      int64_t base_l, int64_t base_child, int nchild,
-                      const int32_t* __restrict__ rank, const int64_t* __restrict__ voff,
-                      const int64_t* __restrict__ utoff, const typename A::S* __restrict__ ops,
-                      typename A::V* __restrict__ v) {
-    using V = typename A::V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* part = reinterpret_cast<V*>(smem_raw);
-    const int64_t t = blockIdx.x;
-    if (t >= ntask) return;
-    const int64_t s = tasks[t];
-    const int64_t b = s / box_total, X = s - b * box_total - base_l;
-    const int r = rank[s];
-    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-    const int nwarp = blockDim.x / kWarp;
-    for (int j0 = 0; j0 < r; j0 += kWarp) {
-        const int j = j0 + lane;
-        V acc = A::zero();
-        for (int c = 0; c < nchild; ++c) {
-            const int64_t sc = b * box_total + base_child + X * nchild + c;
-            const int rc = rank[sc];
-            const typename A::S* Ut = ops + utoff[sc];
-            const V* vc = v + voff[sc];
-            if (j < r) {
-#pragma unroll 4
-                for (int i = warp; i < rc; i += nwarp) acc = A::mac(acc, Ut[int64_t(i) * r + j], vc[i]);
-            }
-        }
-        if (j < r) part[warp * r + j] = acc;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-        V acc = part[j];
-        for (int w = 1; w < nwarp; ++w) acc = A::add(acc, part[w * r + j]);
-        v[voff[s] + j] = acc;
-    }
-}
-
-// ---- block-row GEMV: M2L and the stored near field (+ fused L2P) -------------
-template <class A>
+// ---- block-row GEMV: M2L, L2L and the stored near field (+ fused L2P) ---------
+// One CTA (8 warps) per task.  The gathered coefficients are staged through a
+// 1024-entry shared-memory chunk; each warp owns RW rows (rows warp, warp + 8,
+// ...) and streams them with 16-byte loads, so one staged coefficient feeds RW
+// multiply-adds and each lane keeps RW independent loads in flight.  Segments
+// are sorted by column (seg_col = first column of each segment).
+template <class A, int RW>
 __global__ void __launch_bounds__(256) k_rowgemv(
     int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
     const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
     const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
-    const int32_t* __restrict__ seg_len, const typename A::S* __restrict__ ops,
-    typename A::V* __restrict__ vec) {
+    const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
+    const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate) {
     using V = typename A::V;
     using L = typename A::L;
     constexpr int W = A::W;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* xg = reinterpret_cast<V*>(smem_raw);
+    constexpr int C = 1024;                   // multiple of 32 * W for W = 2 and 4
+    constexpr int NW = 8;
+    __shared__ __align__(16) V xs[C];
     const int64_t t = blockIdx.x;
     if (t >= ntask) return;
     const int kp = kpad[t];
-    int col = 0;
-    for (int64_t e = seg_ptr[t]; e < seg_ptr[t + 1]; ++e) {
-        const V* src = vec + seg_off[e];
-        const int len = seg_len[e];
-        for (int j = threadIdx.x; j < len; j += blockDim.x) xg[col + j] = src[j];
-        col += len;
-    }
-    for (int j = col + threadIdx.x; j < kp; j += blockDim.x) xg[j] = A::zero();
-    __syncthreads();
-    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-    const int nwarp = blockDim.x / kWarp;
     const int nr = rows[t];
+    const int64_t e0 = seg_ptr[t], e1 = seg_ptr[t + 1];
+    const int ktot = (e1 > e0) ? seg_col[e1 - 1] + seg_len[e1 - 1] : 0;
     const typename A::S* Am = ops + aoff[t];
-    const int nv = kp / W;
     V* y = vec + dst[t];
-    for (int row = warp; row < nr; row += nwarp) {
-        const L* arow = reinterpret_cast<const L*>(Am + int64_t(row) * kp);
-        V acc = A::zero();
-#pragma unroll 4
-        for (int k = lane; k < nv; k += kWarp) {
-            const L a = __ldg(arow + k);
-#pragma unroll
-            for (int w = 0; w < W; ++w) acc = A::mac(acc, A::lget(a, w), xg[k * W + w]);
-        }
-        acc = warp_sum<A>(acc);
-        if (lane == 0) y[row] = acc;
-    }
-}
-
-// ---- L2L: u_{X_c} += U~_{X_c X} u_X, one CTA per child ----------------------
-template <class A>
-__global__ void k_l2l(const int64_t* __restrict__ tasks, int64_t ntask, int64_t box_total,
-                      int64_t base_l, int64_t base_parent, int dshift,
-                      const int32_t* __restrict__ rank, const int64_t* __restrict__ voff,
-                      const int64_t* __restrict__ utoff, const typename A::S* __restrict__ ops,
-                      typename A::V* __restrict__ u) {
-    using V = typename A::V;
-    const int64_t t = blockIdx.x;
-    if (t >= ntask) return;
-    const int64_t s = tasks[t];
-    const int64_t b = s / box_total, X = s - b * box_total - base_l;
-    const int64_t sp = b * box_total + base_parent + (X >> dshift);
-    const int rc = rank[s], rp = rank[sp];
-    const typename A::S* Ut = ops + utoff[s];
-    const V* up = u + voff[sp];
-    V* uc = u + voff[s];
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-    const int nwarp = blockDim.x / kWarp;
-    for (int i = warp; i < rc; i += nwarp) {
-        V part = A::zero();
-        for (int j = lane; j < rp; j += kWarp) part = A::mac(part, Ut[int64_t(i) * rp + j], up[j]);
-        part = warp_sum<A>(part);
-        if (lane == 0) uc[i] = A::add(uc[i], part);
+    for (int r0 = 0; r0 < nr; r0 += NW * RW) {
+        V acc[RW];
+        bool ok[RW];
+        const L* arow[RW];
+#pragma unroll
+        for (int w = 0; w < RW; ++w) {
+            acc[w] = A::zero();
+            const int row = r0 + warp + NW * w;
+            ok[w] = row < nr;
+            arow[w] = reinterpret_cast<const L*>(Am + int64_t(ok[w] ? row : 0) * kp);
+        }
+        int64_t ef = e0;                      // first segment not yet fully consumed
+        for (int c0 = 0; c0 < kp; c0 += C) {
+            const int cw = min(C, kp - c0);
+            __syncthreads();
+            while (ef < e1 && seg_col[ef] + seg_len[ef] <= c0) ++ef;
+            for (int64_t e = ef; e < e1; ++e) {
+                const int sc = seg_col[e];
+                if (sc >= c0 + cw) break;
+                const int lo = max(sc, c0), hi = min(sc + seg_len[e], c0 + cw);
+                const V* src = vec + seg_off[e] + (lo - sc);
+                for (int j = threadIdx.x; j < hi - lo; j += blockDim.x) xs[lo - c0 + j] = src[j];
+            }
+            for (int j = max(ktot - c0, 0) + threadIdx.x; j < cw; j += blockDim.x) xs[j] = A::zero();
+            __syncthreads();
+            const int nv = cw / W, k0 = c0 / W;
+            for (int k = lane; k < nv; k += kWarp) {
+                V xv[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) xv[w] = xs[k * W + w];
+                L a[RW];
+#pragma unroll
+                for (int w = 0; w < RW; ++w)
+                    if (ok[w]) a[w] = __ldg(arow[w] + k0 + k);
+#pragma unroll
+                for (int w = 0; w < RW; ++w)
+                    if (ok[w]) {
+#pragma unroll
+                        for (int z = 0; z < W; ++z) acc[w] = A::mac(acc[w], A::lget(a[w], z), xv[z]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < RW; ++w) {
+            if (!ok[w]) continue;
+            const V sum = warp_sum<A>(acc[w]);
+            const int row = r0 + warp + NW * w;
+            if (lane == 0) y[row] = accumulate ? A::add(y[row], sum) : sum;
+        }
     }
 }
 
