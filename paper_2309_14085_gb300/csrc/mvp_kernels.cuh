@@ -181,10 +181,10 @@ __global__ void k_scatter(const typename A::V* __restrict__ phi, const int64_t* 
 
 // ---- block-row GEMV: M2L, L2L and the stored near field (+ fused L2P) ---------
 // One CTA (8 warps) per task.  The gathered coefficients are staged through a
-// 1024-entry shared-memory chunk; each warp owns RW rows (rows warp, warp + 8,
-// ...) and streams them with 16-byte loads, so one staged coefficient feeds RW
-// multiply-adds and each lane keeps RW independent loads in flight.  Segments
-// are sorted by column (seg_col = first column of each segment).
+// 32 KB shared-memory chunk; each warp owns RW rows (rows warp, warp + 8, ...)
+// and streams them with 16-byte loads, two k-steps per iteration, so one staged
+// coefficient feeds RW multiply-adds and each lane keeps 2 RW independent loads
+// in flight.  Segments are sorted by column (seg_col = first column of each).
 template <class A, int RW>
 __global__ void __launch_bounds__(256) k_rowgemv(
     int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) k_rowgemv(
     using V = typename A::V;
     using L = typename A::L;
     constexpr int W = A::W;
-    constexpr int C = 1024;                   // multiple of 32 * W for W = 2 and 4
+    constexpr int C = 4096 * 8 / int(sizeof(V));   // 32 KB of staged coefficients
     constexpr int NW = 8;
     __shared__ __align__(16) V xs[C];
     const int64_t t = blockIdx.x;
@@ -233,19 +233,30 @@ __global__ void __launch_bounds__(256) k_rowgemv(
             for (int j = max(ktot - c0, 0) + threadIdx.x; j < cw; j += blockDim.x) xs[j] = A::zero();
             __syncthreads();
             const int nv = cw / W, k0 = c0 / W;
-            for (int k = lane; k < nv; k += kWarp) {
-                V xv[W];
+            // two k-steps per iteration: 2 * RW independent 16-byte loads per lane
+            for (int k = lane; k < nv; k += 2 * kWarp) {
+                const bool two = k + kWarp < nv;
+                L a0[RW], a1[RW];
 #pragma unroll
-                for (int w = 0; w < W; ++w) xv[w] = xs[k * W + w];
-                L a[RW];
+                for (int w = 0; w < RW; ++w) {
+                    if (ok[w]) a0[w] = __ldg(arow[w] + k0 + k);
+                    if (ok[w] && two) a1[w] = __ldg(arow[w] + k0 + k + kWarp);
+                }
+                V x0[W], x1[W];
 #pragma unroll
-                for (int w = 0; w < RW; ++w)
-                    if (ok[w]) a[w] = __ldg(arow[w] + k0 + k);
+                for (int z = 0; z < W; ++z) {
+                    x0[z] = xs[k * W + z];
+                    x1[z] = two ? xs[(k + kWarp) * W + z] : A::zero();
+                }
 #pragma unroll
                 for (int w = 0; w < RW; ++w)
                     if (ok[w]) {
 #pragma unroll
-                        for (int z = 0; z < W; ++z) acc[w] = A::mac(acc[w], A::lget(a[w], z), xv[z]);
+                        for (int z = 0; z < W; ++z) acc[w] = A::mac(acc[w], A::lget(a0[w], z), x0[z]);
+                        if (two) {
+#pragma unroll
+                            for (int z = 0; z < W; ++z) acc[w] = A::mac(acc[w], A::lget(a1[w], z), x1[z]);
+                        }
                     }
             }
         }

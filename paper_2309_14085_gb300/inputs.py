@@ -21,6 +21,8 @@ WORKLOADS = {
     "c2_3d_invr_n262144": dict(number=2, N=262144, d=3, kernel="invr", n_max=64, eps=1e-6, nrhs=1),
     "c2_3d_invr_n262144_eps1e-9": dict(number=2, N=262144, d=3, kernel="invr", n_max=64,
                                         eps=1e-9, nrhs=1),
+    # the same kernel and leaf size one level shallower (kappa 3): the profiling case
+    "c2s_3d_invr_n32768": dict(number=2, N=32768, d=3, kernel="invr", n_max=64, eps=1e-6, nrhs=1),
     # 2D log r, N = 2^20, kappa 7, 64 right-hand sides
     "c3_2d_log_n1048576": dict(number=3, N=1 << 20, d=2, kernel="log2d", n_max=64, eps=1e-10,
                                 nrhs=64),
