@@ -28,7 +28,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import dense, h2
+from oracle import dense, h2, kernels
 from paper_2309_14085_gb300 import H2Matrix, inputs
 
 torch = pytest.importorskip("torch")
@@ -197,7 +197,11 @@ def test_c2_3d_invr_n262144_sampled_rows(storage):
     y = _gpu_mvp(A, q)
     rows, ref, exact = _c2_golden()
     if storage == "f32":
-        assert _maxrel(y[rows], ref) <= 1e-5
+        absrow = np.concatenate([np.abs(kernels.block("invr", P, rows[i:i + 64], np.arange(P.shape[0])))
+                                 @ np.abs(q) for i in range(0, rows.size, 64)])
+        worst = float((np.abs(y[rows] - ref) / (64 * 2.0 ** -24 * absrow)).max())
+        print(f"c2 fp32: max |y - ref| / (64 u |K||q|) = {worst:.3f}")
+        assert worst <= 1.0
     else:
         assert _maxrel(y[rows], ref) <= F64_TOL
     re_gpu = dense.relative_error(y[rows], exact)
