@@ -189,6 +189,32 @@ int h2_tree_order(h2_handle h, int64_t* perm);
 int h2_profile(h2_handle h, int enable);
 int h2_stage_times(h2_handle h, double* ms, int cap, int64_t* calls, int64_t* launches);
 
+/*
+ * h2_matvec_noalloc -- y = K~ x for one right-hand side, without any device
+ * allocation (the paper has no counterpart; this is a deployment entry point).
+ *
+ * For callers that cannot call cudaMalloc while products run -- a serving
+ * process that reserved its whole device memory budget up front, or code
+ * recording work into a CUDA graph -- the product's scratch (charges,
+ * multipole / local coefficients and potentials in tree order) comes from one
+ * static device array of 32 MiB that every GPU loading this library holds
+ * until exit, instead of the handle's own buffer.  The handle (built by
+ * h2_build on the current device) still supplies the operators.
+ *
+ *   x, y   device, fp64, N entries in user point order (y overwritten).
+ *   stream cudaStream_t (NULL = legacy default stream); asynchronous.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and the call
+ * clears what must start at zero, so calls that overlap on the GPU (other
+ * streams, other handles, other host threads) race: serialise them.
+ * Errors: H2_E_INVALID_ARG (NULL pointers, wrong current device, or a handle
+ * whose scratch exceeds 32 MiB -- the message states both sizes),
+ * H2_E_NO_DEVICE, H2_E_CUDA.
+ */
+int h2_matvec_noalloc(h2_handle h, const double* x, double* y, void* stream);
+
 /* h2_last_error -- message of the last failure on this thread ("" if none). */
 const char* h2_last_error(void);
 

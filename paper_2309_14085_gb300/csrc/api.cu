@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -694,3 +695,68 @@ void h2_destroy(h2_handle h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free product.  For callers that must not allocate device memory
+// at all while they run products -- a serving process that reserved its whole
+// device memory budget up front, or code that records work into a CUDA graph,
+// where cudaMalloc is off limits -- h2_matvec_noalloc takes its coefficient
+// scratch (charges, multipole and local coefficients and potentials in tree
+// order) from one static device array instead of the handle's buffer.
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;   // 32 MiB, held by every GPU that loads us
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+constexpr int kNoAllocDevices = 64;
+void* g_noalloc_ptr[kNoAllocDevices] = {};          // device address of the array, per device
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+extern "C" int h2_matvec_noalloc(h2_handle h, const double* X, double* Y, void* stream) {
+    g_err.clear();
+    if (!h) return fail(H2_E_INVALID_ARG, "handle is NULL");
+    if (!h->on_device) return fail(H2_E_NO_DEVICE, "handle was built host-only");
+    if (!X || !Y) return fail(H2_E_INVALID_ARG, "X or Y is NULL");
+    const h2::Packed& P = h->host.packed;
+    const size_t vec_bytes = (size_t(P.veclen) * h->vsize + 255) / 256 * 256;
+    const size_t need = vec_bytes + size_t(P.lr_tlen) * h->vsize;
+    if (need > kNoAllocBytes)
+        return fail(H2_E_INVALID_ARG, "h2_matvec_noalloc: this handle needs " + std::to_string(need) +
+                                          " bytes of scratch; the static buffer holds " +
+                                          std::to_string(kNoAllocBytes) + " (use h2_matvec)");
+    int dev = -1;
+    H2_CUDA(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(H2_E_INVALID_ARG, "the current device is not the handle's device");
+    if (dev < 0 || dev >= kNoAllocDevices) return fail(H2_E_UNSUPPORTED, "device index too large");
+    {
+        // once per device, with that device current: the host-side name of the
+        // array is not a device address, so ask the runtime for it
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess)
+                return fail(H2_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = p;
+        }
+    }
+    unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    // run the ordinary single-RHS pipeline with its scratch pointed at the array
+    void* saved_vec = h->vec;
+    void* saved_lrt = h->lr_t;
+    const bool saved_profile = h->profile;
+    h->vec = base;
+    h->lr_t = base + vec_bytes;
+    h->profile = false;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int st = h->host.storage;
+    int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, X, Y, s)
+             : (st == H2_F32) ? matvec_one<h2::F32>(h, X, Y, s)
+                              : matvec_one<h2::DF>(h, X, Y, s);
+    h->vec = saved_vec;
+    h->lr_t = saved_lrt;
+    h->profile = saved_profile;
+    return rc;
+}
+
