@@ -32,6 +32,11 @@ UNIT = "points*RHS/s"
 KERNEL_NAMES = {"log2d": "log r (2D)", "invr": "1/r (3D)", "imq": "inverse multiquadric",
                 "matern12": "exp(-r)"}
 VARIANT_NAMES = {"h2star": "H2*(b+t)", "h2plush": "(H2+H)*", "h2sqrt": "H2_sqrt(d)(b)"}
+# DRAM traffic / algorithmic bytes of the M2L block-row launch, from one ncu
+# capture of the current kernel (profiles/k_rowgemv_m2l_c2s_3d_invr_n32768.md);
+# traffic grows with the stored blocks, so a full launch's traffic is this
+# ratio times its algorithmic bytes.
+M2L_TRAFFIC_RATIO = {"df64": 0.991, "f64": 0.995, "f32": 0.999}
 
 
 def _peaks():
@@ -228,9 +233,12 @@ def bench_ours(args, rank, world):
             alg = info["bytes_leaf_rows"] + (info["leaf_src_coeffs"] + N) * ts
         sec = per[dom] / 1e3
         ach = alg / sec / 1e9
+        traffic = None
+        if dom == "m2l" and args.variant == "h2star" and args.storage in M2L_TRAFFIC_RATIO:
+            traffic = int(M2L_TRAFFIC_RATIO[args.storage] * alg)
         roof.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s",
-                    frac=round(ach / hbm, 4), traffic=None, alg_bytes=alg,
-                    peak_source=f"{how} hbm_gbs")
+                    frac=round(ach / hbm, 4), traffic=traffic, alg_bytes=alg,
+                    peak_source=f"{how} hbm_gbs (of measured)")
         if args.storage == "f64":
             # one fp64 multiply-add per stored 8-byte entry: the FP64 pipe bound
             fma = alg / 8 / sec / 1e12
@@ -278,6 +286,8 @@ def main():
     ap.add_argument("--storage", default="f64", choices=["f64", "df64", "f32"])
     ap.add_argument("--variant", default="h2star", choices=list(VARIANT_NAMES))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--also", default="df64,f32",
+                    help="other storage modes measured in the same run (comma list, '' for none)")
     ap.add_argument("--oracle-child", nargs=2, default=None)
     args = ap.parse_args()
     if args.oracle_child:
@@ -319,6 +329,20 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
     out, w = bench_ours(args, rank, world)
+    if args.also:
+        extra = {}
+        for st in [x for x in args.also.split(",") if x and x != args.storage]:
+            a2 = argparse.Namespace(**vars(args))
+            a2.storage = st
+            a2.steps = max(3, min(args.steps, 50))
+            o2, _ = bench_ours(a2, rank, world)
+            r2 = o2["roofline"]
+            extra[st] = {"value": o2["value"], "ms_per_step": o2["ms_per_step"],
+                         "dominant": r2["kernel"], "frac": r2.get("frac"),
+                         "achieved_gbs": r2.get("achieved"), "stage_ms": r2["stage_ms"],
+                         "e2e": o2["e2e"]["value"], "clocks": o2["clocks"],
+                         "gpu_launches": o2["gpu_launches"]}
+        out["other_storage"] = extra
     if rank == 0:
         cb = run_oracle_rows(args.workload, args.cpu_seconds)
         out["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],
