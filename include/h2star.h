@@ -189,6 +189,46 @@ int h2_tree_order(h2_handle h, int64_t* perm);
 int h2_profile(h2_handle h, int enable);
 int h2_stage_times(h2_handle h, double* ms, int cap, int64_t* calls, int64_t* launches);
 
+/* Result of a solve, filled by h2_gmres. */
+typedef struct {
+    int     converged;         /* 1 if the relative residual reached rtol              */
+    int     iterations;        /* GMRES iterations (Arnoldi steps), all cycles         */
+    int     restarts;          /* restarts of GMRES(restart)                           */
+    int     refinements;       /* outer iterative-refinement steps (0 without h_res)   */
+    int64_t matvecs;           /* products with the solver's handle                    */
+    int64_t matvecs_residual;  /* products with the residual handle                    */
+    double  rel_residual;      /* ||b - A x||_2 / ||b||_2, recomputed in fp64 at exit  */
+    double  rel_residual_est;  /* the last GMRES least-squares estimate                */
+    double  seconds;           /* wall time of the call (it synchronises the stream)   */
+} h2_gmres_stats;
+
+/*
+ * h2_gmres -- solve (shift I + scale K~) x = b in fp64 on the device.
+ *
+ * §6 solves the discretised integral equations and RBF systems with GMRES,
+ * the matrix-vector product accelerated by the hierarchical representation,
+ * stopped when the relative residual ||b - A x|| / ||b|| drops below
+ * eps_GMRES.  Here: restarted GMRES(restart) (restart >= maxit gives the
+ * unrestarted method), x0 = 0, classical Gram-Schmidt applied twice, Givens
+ * rotations; the Krylov basis (N x (restart + 1) doubles) is kept in the
+ * handle for later solves.
+ *
+ *   h      handle whose product the GMRES iterations use (any storage).
+ *   h_res  NULL, or a second handle on the same points and device (e.g.
+ *          fp64 storage when h is fp32): then the solve is an iterative
+ *          refinement -- residuals r = b - A x are recomputed in fp64 with
+ *          h_res, each correction comes from GMRES on h -- so it reaches an
+ *          fp64 tolerance while the iterations use the faster product.
+ *   b, x   device, fp64, N entries in user order (x overwritten).
+ *   rtol   relative residual target in (0, 1); restart in [1, 1000]; maxit >= 1
+ *          bounds the GMRES iterations over all cycles and refinements.
+ *   st     nullable; filled also on H2_E_NOT_CONVERGED (x then holds the last
+ *          iterate).  The call synchronises `stream`.
+ * Errors: H2_E_INVALID_ARG, H2_E_NO_DEVICE, H2_E_OOM, H2_E_CUDA, H2_E_NOT_CONVERGED.
+ */
+int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale, const double* b,
+             double* x, double rtol, int restart, int maxit, h2_gmres_stats* st, void* stream);
+
 /*
  * h2_matvec_noalloc -- y = K~ x for one right-hand side, without any device
  * allocation (the paper has no counterpart; this is a deployment entry point).

@@ -24,7 +24,7 @@ VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2}
 STORAGE = {"f64": 0, "f32": 1, "df64": 2}
 NEAR = {None: 0, "fly": 1, "stored": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
-EXPORTED = ("h2_build", "h2_matvec", "h2_info", "h2_get_pivots", "h2_tree_order",
+EXPORTED = ("h2_build", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy")
 
 
@@ -55,6 +55,14 @@ class Stats(ctypes.Structure):
                 ("build_seconds", ctypes.c_double)]
 
 
+class GmresStats(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("matvecs", ctypes.c_int64), ("matvecs_residual", ctypes.c_int64),
+                ("rel_residual", ctypes.c_double), ("rel_residual_est", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
 class H2Error(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"h2 error {code}: {msg}")
@@ -77,6 +85,8 @@ def lib():
                                ctypes.POINTER(BuildOpts), ctypes.POINTER(c_vp)]
         L.h2_matvec.argtypes = [c_vp, c_vp, c_i64, c_vp, c_i64, c_int, c_vp]
         L.h2_info.argtypes = [c_vp, ctypes.POINTER(Stats)]
+        L.h2_gmres.argtypes = [c_vp, c_vp, c_dbl, c_dbl, c_vp, c_vp, c_dbl, c_int, c_int,
+                               ctypes.POINTER(GmresStats), c_vp]
         L.h2_get_pivots.argtypes = [c_vp, c_int, c_int, c_i64, c_vp, c_vp, c_i64,
                                     ctypes.POINTER(c_int)]
         L.h2_tree_order.argtypes = [c_vp, c_vp]
@@ -158,6 +168,27 @@ class H2Matrix:
         if out is not None:
             return out
         return Y.reshape(self.N) if vec else Y
+
+    # -- solves ------------------------------------------------------------------
+    def gmres(self, b, shift=0.0, scale=1.0, rtol=1e-10, restart=100, maxit=1000,
+              residual=None, out=None, stream=None):
+        """x solving (shift I + scale K~) x = b (fp64 CUDA tensor b, shape (N,)).
+
+        `residual`: optional second H2Matrix on the same points (e.g. fp64
+        storage when this one is fp32) for mixed-precision iterative refinement.
+        Returns (x, stats dict); stats["converged"] tells whether rtol was met."""
+        import torch
+        if b.dtype != torch.float64 or not b.is_cuda or b.dim() != 1 or b.shape[0] != self.N:
+            raise ValueError("b must be a float64 CUDA vector of length N")
+        b = b.contiguous()
+        x = torch.empty_like(b) if out is None else out
+        st = GmresStats()
+        rc = lib().h2_gmres(self._h, residual._h if residual is not None else None, shift, scale,
+                            ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), rtol,
+                            restart, maxit, ctypes.byref(st), _stream_ptr(stream))
+        if rc not in (0, -4):
+            _check(rc)
+        return x, {f[0]: getattr(st, f[0]) for f in GmresStats._fields_}
 
     # -- introspection -----------------------------------------------------------
     def info(self):

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -15,6 +17,7 @@
 
 #include "../../include/h2star.h"
 #include "h2_internal.hpp"
+#include "gmres_kernels.cuh"
 #include "mvp_kernels.cuh"
 
 namespace {
@@ -88,6 +91,15 @@ struct h2_handle_s {
     double stage_ms[ST_N] = {};
     int64_t stage_calls = 0;
     int64_t launches = 0;               // kernels launched by h2_matvec
+    // GMRES workspace (grown on demand, kept for later solves)
+    int gm_cap = -1;                    // restart length the workspace holds
+    double* gm_V = nullptr;             // N x (m + 1) Krylov basis
+    double* gm_w = nullptr;             // N
+    double* gm_r = nullptr;             // N
+    double* gm_d = nullptr;             // N (refinement correction)
+    double* gm_partial = nullptr;       // kDotBlocks x (m + 1)
+    double* gm_h = nullptr;             // m + 1
+    std::vector<void*> gm_allocs;
 };
 
 namespace {
@@ -689,6 +701,7 @@ void h2_destroy(h2_handle h) {
     if (h->on_device || !h->allocs.empty()) {
         cudaDeviceSynchronize();
         for (void* p : h->allocs) cudaFree(p);
+        for (void* p : h->gm_allocs) cudaFree(p);
         for (auto& e : h->ev_pool) cudaEventDestroy(e);
     }
     delete h;
@@ -758,5 +771,237 @@ extern "C" int h2_matvec_noalloc(h2_handle h, const double* X, double* Y, void* 
     h->lr_t = saved_lrt;
     h->profile = saved_profile;
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES (§6 solves K sigma = f with unrestarted GMRES and the fast MVP) and
+// mixed-precision iterative refinement, all vectors in fp64 on the device.
+namespace {
+
+int gm_alloc(h2_handle h, double** p, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(double));
+    if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    h->gm_allocs.push_back(q);
+    *p = static_cast<double*>(q);
+    return H2_OK;
+}
+
+int gm_workspace(h2_handle h, int m) {
+    if (h->gm_cap >= m) return H2_OK;
+    for (void* p : h->gm_allocs) cudaFree(p);
+    h->gm_allocs.clear();
+    h->gm_cap = -1;
+    const size_t N = size_t(h->host.tree.N);
+    H2_TRY(gm_alloc(h, &h->gm_V, N * size_t(m + 1)));
+    H2_TRY(gm_alloc(h, &h->gm_w, N));
+    H2_TRY(gm_alloc(h, &h->gm_r, N));
+    H2_TRY(gm_alloc(h, &h->gm_d, N));
+    H2_TRY(gm_alloc(h, &h->gm_partial, size_t(h2::kDotBlocks) * (m + 1)));
+    H2_TRY(gm_alloc(h, &h->gm_h, size_t(m + 1)));
+    h->gm_cap = m;
+    return H2_OK;
+}
+
+// host out[i] = V[:, i] . w for i < nvec
+int gm_dots(h2_handle h, const double* V, int64_t ldv, int nvec, const double* w, double* out,
+            cudaStream_t s) {
+    const int64_t N = h->host.tree.N;
+    h2::k_multidot<<<h2::kDotBlocks, h2::kDotThreads, 0, s>>>(V, ldv, nvec, w, N, h->gm_partial);
+    h2::k_reduce_partials<<<nblocks(nvec, 128), 128, 0, s>>>(h->gm_partial, h2::kDotBlocks, nvec, h->gm_h);
+    H2_CUDA(cudaMemcpyAsync(out, h->gm_h, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    return H2_OK;
+}
+
+int gm_norm(h2_handle h, const double* w, double* nrm, cudaStream_t s) {
+    double t = 0.0;
+    H2_TRY(gm_dots(h, w, 0, 1, w, &t, s));
+    *nrm = std::sqrt(std::max(t, 0.0));
+    return H2_OK;
+}
+
+// y = shift x + scale K~ x
+int gm_apply(h2_handle h, double shift, double scale, const double* x, double* y, cudaStream_t s) {
+    const int st = h->host.storage;
+    int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, x, y, s)
+             : (st == H2_F32) ? matvec_one<h2::F32>(h, x, y, s)
+                              : matvec_one<h2::DF>(h, x, y, s);
+    if (rc != H2_OK) return rc;
+    const int64_t N = h->host.tree.N;
+    h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(shift, x, scale, y, N);
+    return H2_OK;
+}
+
+// Restarted GMRES(m) on A = shift I + scale K~(h), from the initial guess in x.
+// Orthogonalisation: classical Gram-Schmidt applied twice (two host reads of
+// the projections per iteration).  Stops when the least-squares residual
+// estimate drops below rtol * bnorm, or after maxit iterations.
+int gm_solve(h2_handle h, double shift, double scale, const double* b, double bnorm, double* x,
+             double rtol, int m, int maxit, cudaStream_t s, int* iters, int* restarts,
+             int64_t* matvecs, double* est, bool* converged) {
+    const int64_t N = h->host.tree.N;
+    double* V = h->gm_V;
+    double* w = h->gm_w;
+    std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), hv(m + 1), hv2(m + 1), y(m);
+    *converged = false;
+    // r = b - A x into V[:, 0]
+    H2_TRY(gm_apply(h, shift, scale, x, w, s));
+    (*matvecs)++;
+    h2::k_axpbyz<<<nblocks(N, 256), 256, 0, s>>>(1.0, b, -1.0, w, V, N);
+    double beta = 0.0;
+    H2_TRY(gm_norm(h, V, &beta, s));
+    *est = beta / bnorm;
+    if (beta <= rtol * bnorm) { *converged = true; return H2_OK; }
+    while (*iters < maxit) {
+        h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(0.0, V, 1.0 / beta, V, N);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jl = -1;
+        for (int j = 0; j < m && *iters < maxit; ++j) {
+            H2_TRY(gm_apply(h, shift, scale, V + int64_t(j) * N, w, s));
+            (*matvecs)++;
+            H2_TRY(gm_dots(h, V, N, j + 1, w, hv.data(), s));
+            H2_CUDA(cudaMemcpyAsync(h->gm_h, hv.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
+            h2::k_gemv_cols<<<nblocks(N, 256), 256, 0, s>>>(V, N, j + 1, h->gm_h, -1.0, w, N);
+            H2_TRY(gm_dots(h, V, N, j + 1, w, hv2.data(), s));
+            H2_CUDA(cudaMemcpyAsync(h->gm_h, hv2.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
+            h2::k_gemv_cols<<<nblocks(N, 256), 256, 0, s>>>(V, N, j + 1, h->gm_h, -1.0, w, N);
+            for (int i = 0; i <= j; ++i) H[size_t(i) * m + j] = hv[i] + hv2[i];
+            double hn = 0.0;
+            H2_TRY(gm_norm(h, w, &hn, s));
+            H[size_t(j + 1) * m + j] = hn;
+            if (hn > 0.0)
+                h2::k_axpbyz<<<nblocks(N, 256), 256, 0, s>>>(1.0 / hn, w, 0.0, w, V + int64_t(j + 1) * N, N);
+            for (int i = 0; i < j; ++i) {
+                const double h0 = H[size_t(i) * m + j], h1 = H[size_t(i + 1) * m + j];
+                H[size_t(i) * m + j] = cs[i] * h0 + sn[i] * h1;
+                H[size_t(i + 1) * m + j] = -sn[i] * h0 + cs[i] * h1;
+            }
+            const double a = H[size_t(j) * m + j], c = H[size_t(j + 1) * m + j];
+            const double den = std::hypot(a, c);
+            cs[j] = den > 0 ? a / den : 1.0;
+            sn[j] = den > 0 ? c / den : 0.0;
+            H[size_t(j) * m + j] = den;
+            H[size_t(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            (*iters)++;
+            jl = j;
+            *est = std::fabs(g[j + 1]) / bnorm;
+            if (std::fabs(g[j + 1]) <= rtol * bnorm || hn == 0.0) break;
+        }
+        if (jl < 0) break;
+        for (int i = jl; i >= 0; --i) {
+            double t = g[i];
+            for (int k = i + 1; k <= jl; ++k) t -= H[size_t(i) * m + k] * y[k];
+            y[i] = H[size_t(i) * m + i] != 0.0 ? t / H[size_t(i) * m + i] : 0.0;
+        }
+        H2_CUDA(cudaMemcpyAsync(h->gm_h, y.data(), sizeof(double) * (jl + 1), cudaMemcpyHostToDevice, s));
+        h2::k_gemv_cols<<<nblocks(N, 256), 256, 0, s>>>(V, N, jl + 1, h->gm_h, 1.0, x, N);
+        if (*est <= rtol) { *converged = true; break; }
+        if (*iters >= maxit) break;
+        // restart from the recomputed residual
+        (*restarts)++;
+        H2_TRY(gm_apply(h, shift, scale, x, w, s));
+        (*matvecs)++;
+        h2::k_axpbyz<<<nblocks(N, 256), 256, 0, s>>>(1.0, b, -1.0, w, V, N);
+        H2_TRY(gm_norm(h, V, &beta, s));
+        *est = beta / bnorm;
+        if (beta <= rtol * bnorm) { *converged = true; break; }
+    }
+    H2_CUDA(cudaGetLastError());
+    return H2_OK;
+}
+
+}  // namespace
+
+extern "C" int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale, const double* b,
+                        double* x, double rtol, int restart, int maxit, h2_gmres_stats* st,
+                        void* stream) {
+    g_err.clear();
+    if (!h || !b || !x) return fail(H2_E_INVALID_ARG, "NULL argument");
+    if (!h->on_device || (h_res && !h_res->on_device))
+        return fail(H2_E_NO_DEVICE, "handle was built host-only");
+    if (h_res && (h_res->host.tree.N != h->host.tree.N || h_res->device != h->device))
+        return fail(H2_E_INVALID_ARG, "the residual handle has another N or device");
+    if (!(rtol > 0.0 && rtol < 1.0)) return fail(H2_E_INVALID_ARG, "rtol must be in (0, 1)");
+    if (restart < 1 || restart > 1000 || maxit < 1) return fail(H2_E_INVALID_ARG, "restart or maxit out of range");
+    if (!std::isfinite(shift) || !std::isfinite(scale)) return fail(H2_E_INVALID_ARG, "shift / scale not finite");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t N = h->host.tree.N;
+    const bool saved_profile = h->profile;
+    h->profile = false;
+    struct Restore {
+        h2_handle h;
+        bool p;
+        ~Restore() { h->profile = p; }
+    } restore{h, saved_profile};
+    H2_TRY(gm_workspace(h, restart));
+    h2_gmres_stats S;
+    std::memset(&S, 0, sizeof(S));
+    double bnorm = 0.0;
+    H2_TRY(gm_norm(h, b, &bnorm, s));
+    H2_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+    if (bnorm == 0.0) {
+        S.converged = 1;
+        if (st) *st = S;
+        return H2_OK;
+    }
+    int iters = 0, restarts = 0;
+    int64_t mv = 0, mv_res = 0;
+    double est = 1.0;
+    bool conv = false;
+    if (!h_res || h_res == h) {
+        H2_TRY(gm_solve(h, shift, scale, b, bnorm, x, rtol, restart, maxit, s, &iters, &restarts, &mv,
+                        &est, &conv));
+        // the true relative residual with the solver's operator
+        H2_TRY(gm_apply(h, shift, scale, x, h->gm_r, s));
+        mv++;
+        h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(1.0, b, -1.0, h->gm_r, N);
+        double rn = 0.0;
+        H2_TRY(gm_norm(h, h->gm_r, &rn, s));
+        S.rel_residual = rn / bnorm;
+    } else {
+        // iterative refinement: residual r = b - A_res x in fp64 with h_res, correction
+        // from GMRES on the faster operator of h; the inner tolerance follows the
+        // inner operator's precision
+        const double floor_inner = h->host.storage == H2_F32 ? 1e-5 : 1e-10;
+        double* r = h->gm_r;
+        double* dx = h->gm_d;
+        H2_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        double rn = bnorm;
+        for (int outer = 0; outer < 30; ++outer) {
+            if (rn <= rtol * bnorm) { conv = true; break; }
+            if (iters >= maxit) break;
+            const double inner = std::max(floor_inner, 0.5 * rtol * bnorm / rn);
+            H2_CUDA(cudaMemsetAsync(dx, 0, sizeof(double) * N, s));
+            bool c2 = false;
+            double e2 = 1.0;
+            H2_TRY(gm_solve(h, shift, scale, r, rn, dx, inner, restart, maxit - iters, s, &iters,
+                            &restarts, &mv, &e2, &c2));
+            h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(1.0, dx, 1.0, x, N);
+            H2_TRY(gm_apply(h_res, shift, scale, x, r, s));
+            mv_res++;
+            h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(1.0, b, -1.0, r, N);
+            H2_TRY(gm_norm(h, r, &rn, s));
+            S.refinements++;
+            est = e2;
+        }
+        if (rn <= rtol * bnorm) conv = true;
+        S.rel_residual = rn / bnorm;
+    }
+    H2_CUDA(cudaStreamSynchronize(s));
+    S.converged = conv ? 1 : 0;
+    S.iterations = iters;
+    S.restarts = restarts;
+    S.matvecs = mv;
+    S.matvecs_residual = mv_res;
+    S.rel_residual_est = est;
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (st) *st = S;
+    if (!conv) return fail(H2_E_NOT_CONVERGED, "GMRES stopped at maxit before reaching rtol");
+    return H2_OK;
 }
 
