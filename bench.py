@@ -273,7 +273,46 @@ def bench_ours(args, rank, world):
         "gpu_launches": int(launches),   # kernels of the profiled pass = of the timed region
         "roofline": roof,
     }
+    args._handles = getattr(args, "_handles", {})
+    args._handles[args.storage] = A
     return out, w
+
+
+def bench_gmres(handles, w, nsolve=10, rtol=1e-8):
+    """Latency of solves (I + K~/N) x = b to rtol: plain fp64 GMRES and fp32
+    iterations refined with fp64 residuals (same points, same right-hand sides)."""
+    import torch
+    N = w["N"]
+    out = {"system": "(I + K/N) x = b, b ~ N(0,1), x0 = 0", "rtol": rtol, "solves": nsolve}
+    forms = []
+    if "f64" in handles:
+        forms.append(("fp64", handles["f64"], None))
+    if "f32" in handles and "f64" in handles:
+        forms.append(("fp32_refined_fp64", handles["f32"], handles["f64"]))
+    if "df64" in handles and "f64" in handles:
+        forms.append(("df64_refined_fp64", handles["df64"], handles["f64"]))
+    for name, A, R in forms:
+        lat, its, res = [], [], []
+        for k in range(nsolve + 1):
+            b = torch.tensor(np.random.default_rng(5000 + k).standard_normal(N), device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, st = A.gmres(b, shift=1.0, scale=1.0 / N, rtol=rtol, restart=50, maxit=500,
+                            residual=R)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if k == 0:
+                continue                     # first solve allocates the Krylov workspace
+            lat.append(dt)
+            its.append(st["iterations"])
+            res.append(st["rel_residual"])
+        lat = np.array(lat)
+        out[name] = {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                     "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                     "solves_per_s": round(float(len(lat) / lat.sum()), 2),
+                     "iterations_median": float(np.median(its)),
+                     "max_rel_residual": float(max(res))}
+    return out
 
 
 def main():
@@ -286,6 +325,7 @@ def main():
     ap.add_argument("--storage", default="f64", choices=["f64", "df64", "f32"])
     ap.add_argument("--variant", default="h2star", choices=list(VARIANT_NAMES))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--gmres-solves", type=int, default=10)
     ap.add_argument("--also", default="df64,f32",
                     help="other storage modes measured in the same run (comma list, '' for none)")
     ap.add_argument("--oracle-child", nargs=2, default=None)
@@ -336,6 +376,7 @@ def main():
             a2.storage = st
             a2.steps = max(3, min(args.steps, 50))
             o2, _ = bench_ours(a2, rank, world)
+            args._handles = a2._handles
             r2 = o2["roofline"]
             extra[st] = {"value": o2["value"], "ms_per_step": o2["ms_per_step"],
                          "dominant": r2["kernel"], "frac": r2.get("frac"),
@@ -343,6 +384,8 @@ def main():
                          "e2e": o2["e2e"]["value"], "clocks": o2["clocks"],
                          "gpu_launches": o2["gpu_launches"]}
         out["other_storage"] = extra
+    if args.gmres_solves > 0:
+        out["gmres"] = bench_gmres(getattr(args, "_handles", {}), w, nsolve=args.gmres_solves)
     if rank == 0:
         cb = run_oracle_rows(args.workload, args.cpu_seconds)
         out["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],
