@@ -143,6 +143,9 @@ def bench_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     w = inputs.workload(args.workload)
+    if args.nrhs:
+        w["nrhs"] = args.nrhs
+        w["q"] = inputs.rhs(w["N"], args.nrhs, 2000 + w["number"])
     N, nrhs = w["N"], w["nrhs"]
     t0 = time.perf_counter()
     A = H2Matrix(w["points"], w["kernel"], leaf_size=w["n_max"], tol=w["eps"],
@@ -326,6 +329,7 @@ def main():
     ap.add_argument("--variant", default="h2star", choices=list(VARIANT_NAMES))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--gmres-solves", type=int, default=10)
+    ap.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS count")
     ap.add_argument("--also", default="df64,f32",
                     help="other storage modes measured in the same run (comma list, '' for none)")
     ap.add_argument("--oracle-child", nargs=2, default=None)

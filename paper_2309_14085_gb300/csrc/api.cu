@@ -59,8 +59,11 @@ struct h2_handle_s {
     // device buffers
     void* ops = nullptr;          // stored entries (double / float / float2)
     void* xs = nullptr;           // coordinates, d x N (on-the-fly near field)
-    void* vec = nullptr;          // [ q | v | u | phi ]
-    void* lr_t = nullptr;         // (H2+H)* scratch V^T q_Y
+    void* vec = nullptr;          // [ q | v | u | phi ] x vec_nrhs (point-major, RHS fastest)
+    void* lr_t = nullptr;         // (H2+H)* scratch V^T q_Y, x vec_nrhs
+    int vec_nrhs = 0;             // right-hand sides the buffers hold
+    void* vec_alloc = nullptr;    // owned allocations of vec / lr_t (regrown for more RHS)
+    void* lrt_alloc = nullptr;
     int64_t* perm = nullptr;
     int64_t* leaf_ptr = nullptr;
     int64_t* near_ptr = nullptr;
@@ -146,6 +149,34 @@ template <> struct Conv<h2::DF> {
     }
 };
 
+// (Re)allocate the coefficient buffers for nrhs right-hand sides.
+int grow_vec(h2_handle h, int nrhs) {
+    if (nrhs <= h->vec_nrhs) return H2_OK;
+    const h2::Packed& P = h->host.packed;
+    if (h->vec_alloc) {
+        cudaDeviceSynchronize();
+        cudaFree(h->vec_alloc);
+        cudaFree(h->lrt_alloc);
+        h->bytes_device -= int64_t(P.veclen * h->vec_nrhs + P.lr_tlen * h->vec_nrhs) * int64_t(h->vsize);
+        h->vec_alloc = h->lrt_alloc = h->vec = h->lr_t = nullptr;
+        h->vec_nrhs = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(size_t(P.veclen) * nrhs * h->vsize, 16));
+    if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    void* q = nullptr;
+    e = cudaMalloc(&q, std::max<size_t>(size_t(P.lr_tlen) * nrhs * h->vsize, 16));
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->vec_alloc = h->vec = p;
+    h->lrt_alloc = h->lr_t = q;
+    h->vec_nrhs = nrhs;
+    h->bytes_device += int64_t(P.veclen * nrhs + P.lr_tlen * nrhs) * int64_t(h->vsize);
+    return H2_OK;
+}
+
 int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize) {
     D.n = R.size();
     H2_TRY(dev_upload(h, &D.dst, R.dst));
@@ -161,19 +192,47 @@ int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize
     return H2_OK;
 }
 
-template <class A, int RW>
-void launch_rows_rw(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate) {
-    h2::k_rowgemv<A, RW><<<unsigned(R.n), 256, 0, s>>>(
+template <class A, int RW, int NR>
+void launch_rows_rw(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate,
+                    int nrhs, int c0) {
+    h2::k_rowgemv<A, RW, NR><<<unsigned(R.n), 256, 0, s>>>(
         R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
-        static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate);
+        static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate, nrhs, c0);
 }
 
+// Largest RHS tile: 16 columns in fp32, 8 in fp64 / double-float.
+template <class A> constexpr int max_tile() { return std::is_same<A, h2::F32>::value ? 16 : 8; }
+
 template <class A>
-void launch_rows(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate) {
+void launch_rows(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate,
+                 int nrhs = 1, int c0 = 0, int nr = 1) {
     if (R.n == 0) return;
-    if (R.rw == 2) launch_rows_rw<A, 2>(R, ops, vec, s, accumulate);
-    else if (R.rw == 8) launch_rows_rw<A, 8>(R, ops, vec, s, accumulate);
-    else launch_rows_rw<A, 4>(R, ops, vec, s, accumulate);
+    constexpr bool f32 = std::is_same<A, h2::F32>::value;
+    switch (nr) {
+        case 16:
+            if constexpr (f32) launch_rows_rw<A, 1, 16>(R, ops, vec, s, accumulate, nrhs, c0);
+            break;
+        case 8:
+            if constexpr (f32) launch_rows_rw<A, 2, 8>(R, ops, vec, s, accumulate, nrhs, c0);
+            else launch_rows_rw<A, 1, 8>(R, ops, vec, s, accumulate, nrhs, c0);
+            break;
+        case 4: launch_rows_rw<A, 2, 4>(R, ops, vec, s, accumulate, nrhs, c0); break;
+        case 2: launch_rows_rw<A, f32 ? 4 : 2, 2>(R, ops, vec, s, accumulate, nrhs, c0); break;
+        default:
+            if (R.rw == 2) launch_rows_rw<A, 2, 1>(R, ops, vec, s, accumulate, nrhs, c0);
+            else if (R.rw == 8) launch_rows_rw<A, 8, 1>(R, ops, vec, s, accumulate, nrhs, c0);
+            else launch_rows_rw<A, 4, 1>(R, ops, vec, s, accumulate, nrhs, c0);
+    }
+}
+
+// Split nrhs columns into tiles of the supported widths, widest first.
+template <class A>
+std::vector<std::pair<int, int>> rhs_tiles(int nrhs) {
+    std::vector<std::pair<int, int>> t;   // (first column, width)
+    int c = 0;
+    for (int w = max_tile<A>(); w >= 1; w /= 2)
+        while (nrhs - c >= w) { t.push_back({c, w}); c += w; }
+    return t;
 }
 
 // Autotuner: for the two large block-row lists (M2L and the stored leaf rows)
@@ -247,8 +306,7 @@ int upload(h2_handle h) {
         H2_TRY(dev_upload(h, &p, xs));
         h->xs = p;
     }
-    H2_TRY(dev_alloc(h, &h->vec, sizeof(V) * std::max<int64_t>(P.veclen, 1)));
-    H2_TRY(dev_alloc(h, &h->lr_t, sizeof(V) * std::max<int64_t>(P.lr_tlen, 1)));
+    H2_TRY(grow_vec(h, 1));
     H2_TRY(dev_upload(h, &h->perm, t.perm));
     H2_TRY(dev_upload(h, &h->leaf_ptr, t.leaf_ptr));
     H2_TRY(dev_upload(h, &h->near_ptr, P.near_ptr));
@@ -298,30 +356,40 @@ int upload(h2_handle h) {
 
 inline unsigned nblocks(int64_t n, int per) { return unsigned((n + per - 1) / per); }
 
-template <typename T, int D, int KIND>
-void launch_leaf(h2_handle h, cudaStream_t s) {
+template <typename T, int D, int KIND, int NR>
+void launch_leaf(h2_handle h, cudaStream_t s, int nrhs, int c0) {
     const h2::Host& H = h->host;
     const h2::Tree& t = H.tree;
     const h2::Packed& P = H.packed;
     const int64_t nleaf = t.nboxes(t.kappa);
     const T* vec = static_cast<const T*>(h->vec);
-    h2::k_leaf_fly<T, D, KIND><<<unsigned(nleaf), 128, 0, s>>>(
+    h2::k_leaf_fly<T, D, KIND, NR><<<unsigned(nleaf), 128, 0, s>>>(
         nleaf, P.nb, P.box_total, P.box_base[t.kappa], h->leaf_ptr, h->near_ptr, h->near_idx,
-        h->rank, h->voff, h->uoff, h->ustride, static_cast<const T*>(h->ops), vec + P.u_base,
-        static_cast<const T*>(h->xs), t.N, vec + P.q_base, static_cast<T*>(h->vec) + P.phi_base,
-        T(H.kern.param), T(H.kern.diag()));
+        h->rank, h->voff, h->uoff, h->ustride, static_cast<const T*>(h->ops), vec + P.u_base * nrhs,
+        static_cast<const T*>(h->xs), t.N, vec + P.q_base * nrhs,
+        static_cast<T*>(h->vec) + P.phi_base * nrhs, T(H.kern.param), T(H.kern.diag()), nrhs, c0);
 }
 
-template <typename T, int D>
-void launch_leaf_d(h2_handle h, cudaStream_t s) {
-    switch (h->host.kern.kind) {
-        case 0: launch_leaf<T, D, 0>(h, s); break;
-        case 1: launch_leaf<T, D, 1>(h, s); break;
-        case 2: launch_leaf<T, D, 2>(h, s); break;
-        default: launch_leaf<T, D, 3>(h, s); break;
+template <typename T, int D, int KIND>
+void launch_leaf_nr(h2_handle h, cudaStream_t s, int nrhs, int c0, int nr) {
+    switch (nr) {
+        case 16: launch_leaf<T, D, KIND, 16>(h, s, nrhs, c0); break;
+        case 8: launch_leaf<T, D, KIND, 8>(h, s, nrhs, c0); break;
+        case 4: launch_leaf<T, D, KIND, 4>(h, s, nrhs, c0); break;
+        case 2: launch_leaf<T, D, KIND, 2>(h, s, nrhs, c0); break;
+        default: launch_leaf<T, D, KIND, 1>(h, s, nrhs, c0); break;
     }
 }
 
+template <typename T, int D>
+void launch_leaf_d(h2_handle h, cudaStream_t s, int nrhs, int c0, int nr) {
+    switch (h->host.kern.kind) {
+        case 0: launch_leaf_nr<T, D, 0>(h, s, nrhs, c0, nr); break;
+        case 1: launch_leaf_nr<T, D, 1>(h, s, nrhs, c0, nr); break;
+        case 2: launch_leaf_nr<T, D, 2>(h, s, nrhs, c0, nr); break;
+        default: launch_leaf_nr<T, D, 3>(h, s, nrhs, c0, nr); break;
+    }
+}
 
 void mark(h2_handle h, cudaStream_t s, int stage) {
     if (h->profile) cudaEventRecord(h->ev[stage], s);
@@ -359,9 +427,12 @@ int next_event_set(h2_handle h) {
     return H2_OK;
 }
 
-// One right-hand side: X, Y are single device columns (user order, fp64).
+// nrhs right-hand sides: X, Y are device, column-major N x nrhs (leading
+// dimensions ldx, ldy), user order, fp64.  The coefficient buffers must hold
+// nrhs columns (grow_vec).
 template <class A>
-int matvec_one(h2_handle h, const double* X, double* Y, cudaStream_t s) {
+int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int nrhs,
+               cudaStream_t s) {
     using V = typename A::V;
     using S = typename A::S;
     const h2::Host& H = h->host;
@@ -370,91 +441,86 @@ int matvec_one(h2_handle h, const double* X, double* Y, cudaStream_t s) {
     const int K = t.kappa, d = t.d;
     const S* ops = static_cast<const S*>(h->ops);
     V* vec = static_cast<V*>(h->vec);
-    V* q = vec + P.q_base;
-    V* v = vec + P.v_base;
-    V* u = vec + P.u_base;
-    V* phi = vec + P.phi_base;
-    const int64_t nleaf = t.nboxes(K);
+    V* q = vec + P.q_base * nrhs;
+    V* u = vec + P.u_base * nrhs;
+    V* phi = vec + P.phi_base * nrhs;
     int64_t& nl = h->launches;
+    const auto tiles = rhs_tiles<A>(nrhs);
+    auto rows = [&](const DevRowTasks& R, int accumulate) {
+        if (R.n == 0) return;
+        for (const auto& tl : tiles) {
+            ++nl;
+            launch_rows<A>(R, ops, vec, s, accumulate, nrhs, tl.first, tl.second);
+        }
+    };
 
     mark(h, s, ST_GATHER);
     ++nl;
-    h2::k_gather<A><<<nblocks(t.N, 256), 256, 0, s>>>(X, h->perm, q, t.N);
+    h2::k_gather<A><<<nblocks(t.N * nrhs, 256), 256, 0, s>>>(X, ldx, nrhs, h->perm, q, t.N);
     mark(h, s, ST_P2M);
-    if (h->p2m.n > 0) {
-        ++nl;
-        launch_rows<A>(h->p2m, ops, vec, s, 0);
-    }
+    rows(h->p2m, 0);
     mark(h, s, ST_M2M);
-    for (int l = K - 1; l >= 1; --l) {
-        if (h->m2m[l].n == 0) continue;
-        ++nl;
-        launch_rows<A>(h->m2m[l], ops, vec, s, 0);
-    }
+    for (int l = K - 1; l >= 1; --l) rows(h->m2m[l], 0);
     mark(h, s, ST_M2L);
-    if (P.vlen > 0) cudaMemsetAsync(u, 0, sizeof(V) * P.vlen, s);
-    if (h->m2l.n > 0) {
-        ++nl;
-        launch_rows<A>(h->m2l, ops, vec, s, 0);
-    }
+    if (P.vlen > 0) cudaMemsetAsync(u, 0, sizeof(V) * P.vlen * nrhs, s);
+    rows(h->m2l, 0);
     mark(h, s, ST_L2L);
-    for (int l = 2; l <= K; ++l) {
-        if (h->l2l[l].n == 0) continue;
-        ++nl;
-        launch_rows<A>(h->l2l[l], ops, vec, s, 1);
-    }
+    for (int l = 2; l <= K; ++l) rows(h->l2l[l], 1);
     mark(h, s, ST_LEAF);
     if (P.near_stored) {
         // empty leaves keep phi = 0: clear once, the block rows overwrite the rest
-        cudaMemsetAsync(phi, 0, sizeof(V) * t.N, s);
-        if (h->leaf.n > 0) {
-            ++nl;
-            launch_rows<A>(h->leaf, ops, vec, s, 0);
-        }
+        cudaMemsetAsync(phi, 0, sizeof(V) * t.N * nrhs, s);
+        rows(h->leaf, 0);
     } else if constexpr (!std::is_same<A, h2::DF>::value) {
         using T = typename A::V;
-        ++nl;
-        if (d == 2) launch_leaf_d<T, 2>(h, s);
-        else launch_leaf_d<T, 3>(h, s);
+        for (const auto& tl : tiles) {
+            ++nl;
+            if (d == 2) launch_leaf_d<T, 2>(h, s, nrhs, tl.first, tl.second);
+            else launch_leaf_d<T, 3>(h, s, nrhs, tl.first, tl.second);
+        }
     }
     mark(h, s, ST_LOWRANK);
     if constexpr (!std::is_same<A, h2::DF>::value) {
         using T = typename A::V;
         if (H.variant == H2_PLUS_H_STAR && P.lr_tlen > 0) {
             T* tt = static_cast<T*>(h->lr_t);
-            cudaMemsetAsync(tt, 0, sizeof(T) * P.lr_tlen, s);
+            cudaMemsetAsync(tt, 0, sizeof(T) * P.lr_tlen * nrhs, s);
             const int chunk = 4096;
-            for (int l = 1; l <= K; ++l) {
-                const int64_t b0 = P.lr_level_ptr[l], nb = P.lr_level_ptr[l + 1] - b0;
-                if (nb == 0) continue;
-                const int64_t maxmy = h->lr_maxm_level[2 * l + 1];
-                for (int64_t off = 0; off < nb; off += 65535) {
-                    const int64_t cnt = std::min<int64_t>(65535, nb - off);
-                    dim3 grid(nblocks(maxmy, chunk), unsigned(cnt));
-                    ++nl;
-                    h2::k_lr_vtq<T><<<grid, 256, 0, s>>>(b0 + off, cnt, h->lr_y0, h->lr_my, h->lr_k,
-                                                         h->lr_voff, h->lr_toff,
-                                                         reinterpret_cast<const T*>(ops), q, tt, chunk);
+            for (int col = 0; col < nrhs; ++col) {
+                for (int l = 1; l <= K; ++l) {
+                    const int64_t b0 = P.lr_level_ptr[l], nb = P.lr_level_ptr[l + 1] - b0;
+                    if (nb == 0) continue;
+                    const int64_t maxmy = h->lr_maxm_level[2 * l + 1];
+                    for (int64_t off = 0; off < nb; off += 65535) {
+                        const int64_t cnt = std::min<int64_t>(65535, nb - off);
+                        dim3 grid(nblocks(maxmy, chunk), unsigned(cnt));
+                        ++nl;
+                        h2::k_lr_vtq<T><<<grid, 256, 0, s>>>(b0 + off, cnt, h->lr_y0, h->lr_my, h->lr_k,
+                                                             h->lr_voff, h->lr_toff,
+                                                             reinterpret_cast<const T*>(ops), q, tt, chunk,
+                                                             nrhs, col);
+                    }
                 }
-            }
-            for (int l = 1; l <= K; ++l) {
-                const int64_t g0 = h->lr_level_gptr[l], ng = h->lr_level_gptr[l + 1] - g0;
-                if (ng == 0) continue;
-                const int64_t maxmx = h->lr_maxm_level[2 * l];
-                for (int64_t off = 0; off < ng; off += 65535) {
-                    const int64_t cnt = std::min<int64_t>(65535, ng - off);
-                    dim3 grid(nblocks(maxmx, 256), unsigned(cnt));
-                    ++nl;
-                    h2::k_lr_ut<T><<<grid, 256, 0, s>>>(g0 + off, cnt, h->lr_gptr, h->lr_x0, h->lr_mx,
-                                                        h->lr_k, h->lr_uoff, h->lr_toff,
-                                                        reinterpret_cast<const T*>(ops), tt, phi);
+                for (int l = 1; l <= K; ++l) {
+                    const int64_t g0 = h->lr_level_gptr[l], ng = h->lr_level_gptr[l + 1] - g0;
+                    if (ng == 0) continue;
+                    const int64_t maxmx = h->lr_maxm_level[2 * l];
+                    for (int64_t off = 0; off < ng; off += 65535) {
+                        const int64_t cnt = std::min<int64_t>(65535, ng - off);
+                        dim3 grid(nblocks(maxmx, 256), unsigned(cnt));
+                        ++nl;
+                        h2::k_lr_ut<T><<<grid, 256, 0, s>>>(g0 + off, cnt, h->lr_gptr, h->lr_x0, h->lr_mx,
+                                                            h->lr_k, h->lr_uoff, h->lr_toff,
+                                                            reinterpret_cast<const T*>(ops), tt, phi,
+                                                            nrhs, col);
+                    }
                 }
             }
         }
     }
     mark(h, s, ST_SCATTER);
     ++nl;
-    h2::k_scatter<A><<<nblocks(t.N, 256), 256, 0, s>>>(phi, h->perm, Y, t.N);
+    h2::k_scatter<A><<<nblocks(t.N * nrhs, 256), 256, 0, s>>>(phi, nrhs, h->perm, Y, ldy, t.N);
     mark(h, s, ST_N);
     H2_CUDA(cudaGetLastError());
     return H2_OK;
@@ -555,20 +621,18 @@ int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
     if (nrhs < 1 || nrhs > 64) return fail(H2_E_INVALID_ARG, "nrhs must be in [1, 64]");
     if (ldx < N || ldy < N) return fail(H2_E_INVALID_ARG, "leading dimension < N");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    for (int c = 0; c < nrhs; ++c) {
-        const double* x = X + int64_t(c) * ldx;
-        double* y = Y + int64_t(c) * ldy;
-        if (h->profile) {
-            int rc = next_event_set(h);
-            if (rc != H2_OK) return rc;
-        }
-        const int st = h->host.storage;
-        int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, x, y, s)
-                 : (st == H2_F32) ? matvec_one<h2::F32>(h, x, y, s)
-                                  : matvec_one<h2::DF>(h, x, y, s);
+    {
+        int rc = grow_vec(h, nrhs);
         if (rc != H2_OK) return rc;
     }
-    return H2_OK;
+    if (h->profile) {
+        int rc = next_event_set(h);
+        if (rc != H2_OK) return rc;
+    }
+    const int st = h->host.storage;
+    return (st == H2_F64)   ? matvec_one<h2::F64>(h, X, ldx, Y, ldy, nrhs, s)
+           : (st == H2_F32) ? matvec_one<h2::F32>(h, X, ldx, Y, ldy, nrhs, s)
+                            : matvec_one<h2::DF>(h, X, ldx, Y, ldy, nrhs, s);
 }
 
 int h2_info(h2_handle h, h2_stats* st) {
@@ -701,6 +765,8 @@ void h2_destroy(h2_handle h) {
     if (h->on_device || !h->allocs.empty()) {
         cudaDeviceSynchronize();
         for (void* p : h->allocs) cudaFree(p);
+        if (h->vec_alloc) cudaFree(h->vec_alloc);
+        if (h->lrt_alloc) cudaFree(h->lrt_alloc);
         for (void* p : h->gm_allocs) cudaFree(p);
         for (auto& e : h->ev_pool) cudaEventDestroy(e);
     }
@@ -764,9 +830,13 @@ extern "C" int h2_matvec_noalloc(h2_handle h, const double* X, double* Y, void* 
     h->profile = false;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int st = h->host.storage;
-    int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, X, Y, s)
-             : (st == H2_F32) ? matvec_one<h2::F32>(h, X, Y, s)
-                              : matvec_one<h2::DF>(h, X, Y, s);
+    const int64_t N = h->host.tree.N;
+    const int saved_nrhs = h->vec_nrhs;
+    h->vec_nrhs = 1;
+    int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, X, N, Y, N, 1, s)
+             : (st == H2_F32) ? matvec_one<h2::F32>(h, X, N, Y, N, 1, s)
+                              : matvec_one<h2::DF>(h, X, N, Y, N, 1, s);
+    h->vec_nrhs = saved_nrhs;
     h->vec = saved_vec;
     h->lr_t = saved_lrt;
     h->profile = saved_profile;
@@ -824,11 +894,11 @@ int gm_norm(h2_handle h, const double* w, double* nrm, cudaStream_t s) {
 // y = shift x + scale K~ x
 int gm_apply(h2_handle h, double shift, double scale, const double* x, double* y, cudaStream_t s) {
     const int st = h->host.storage;
-    int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, x, y, s)
-             : (st == H2_F32) ? matvec_one<h2::F32>(h, x, y, s)
-                              : matvec_one<h2::DF>(h, x, y, s);
-    if (rc != H2_OK) return rc;
     const int64_t N = h->host.tree.N;
+    int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, x, N, y, N, 1, s)
+             : (st == H2_F32) ? matvec_one<h2::F32>(h, x, N, y, N, 1, s)
+                              : matvec_one<h2::DF>(h, x, N, y, N, 1, s);
+    if (rc != H2_OK) return rc;
     h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(shift, x, scale, y, N);
     return H2_OK;
 }

@@ -165,39 +165,52 @@ __device__ __forceinline__ float kernel_r2<float, 3>(float r2, float, float diag
 }
 
 // ---- gather / scatter between user order and tree order --------------------
+// Coefficients of nrhs right-hand sides are stored point-major, RHS fastest:
+// entry (i, c) of a region at region[i * nrhs + c].
 template <class A>
-__global__ void k_gather(const double* __restrict__ X, const int64_t* __restrict__ perm,
-                         typename A::V* __restrict__ q, int64_t N) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < N) q[i] = A::from_double(X[perm[i]]);
+__global__ void k_gather(const double* __restrict__ X, int64_t ldx, int nrhs,
+                         const int64_t* __restrict__ perm, typename A::V* __restrict__ q, int64_t N) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= N * nrhs) return;
+    const int64_t i = t / nrhs;
+    const int c = int(t - i * nrhs);
+    q[t] = A::from_double(X[int64_t(c) * ldx + perm[i]]);
 }
 
 template <class A>
-__global__ void k_scatter(const typename A::V* __restrict__ phi, const int64_t* __restrict__ perm,
-                          double* __restrict__ Y, int64_t N) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < N) Y[perm[i]] = A::to_double(phi[i]);
+__global__ void k_scatter(const typename A::V* __restrict__ phi, int nrhs,
+                          const int64_t* __restrict__ perm, double* __restrict__ Y, int64_t ldy,
+                          int64_t N) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= N * nrhs) return;
+    const int64_t i = t / nrhs;
+    const int c = int(t - i * nrhs);
+    Y[int64_t(c) * ldy + perm[i]] = A::to_double(phi[t]);
 }
 
 // ---- block-row GEMV: M2L, L2L and the stored near field (+ fused L2P) ---------
-// One CTA (8 warps) per task.  The gathered coefficients are staged through a
-// 32 KB shared-memory chunk; each warp owns RW rows (rows warp, warp + 8, ...)
-// and streams them with 16-byte loads, two k-steps per iteration, so one staged
-// coefficient feeds RW multiply-adds and each lane keeps 2 RW independent loads
-// in flight.  Segments are sorted by column (seg_col = first column of each).
-template <class A, int RW>
+// One CTA (8 warps) per task.  The gathered coefficients of an NR-column tile
+// (columns c0 .. c0 + NR - 1 of nrhs) are staged through a 32 KB shared-memory
+// chunk; each warp owns RW rows (rows warp, warp + 8, ...) and streams them
+// with 16-byte loads, two k-steps per iteration, so one loaded operator entry
+// feeds NR multiply-adds and one staged coefficient RW of them, and each lane
+// keeps 2 RW independent loads in flight.  Segments are sorted by column
+// (seg_col = first column of each).
+template <class A, int RW, int NR>
 __global__ void __launch_bounds__(256) k_rowgemv(
     int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
     const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
     const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
     const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
-    const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate) {
+    const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate,
+    int nrhs, int c0) {
     using V = typename A::V;
     using L = typename A::L;
     constexpr int W = A::W;
-    constexpr int C = 4096 * 8 / int(sizeof(V));   // 32 KB of staged coefficients
+    constexpr int C = 4096 * 8 / int(sizeof(V)) / NR;   // staged columns per chunk
     constexpr int NW = 8;
-    __shared__ __align__(16) V xs[C];
+    static_assert(C % (2 * kWarp * W) == 0, "chunk must hold whole warp steps");
+    __shared__ __align__(16) V xs[C * NR];
     const int64_t t = blockIdx.x;
     if (t >= ntask) return;
     const int kp = kpad[t];
@@ -205,35 +218,40 @@ __global__ void __launch_bounds__(256) k_rowgemv(
     const int64_t e0 = seg_ptr[t], e1 = seg_ptr[t + 1];
     const int ktot = (e1 > e0) ? seg_col[e1 - 1] + seg_len[e1 - 1] : 0;
     const typename A::S* Am = ops + aoff[t];
-    V* y = vec + dst[t];
+    V* y = vec + dst[t] * nrhs + c0;
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     for (int r0 = 0; r0 < nr; r0 += NW * RW) {
-        V acc[RW];
+        V acc[RW][NR];
         bool ok[RW];
         const L* arow[RW];
 #pragma unroll
         for (int w = 0; w < RW; ++w) {
-            acc[w] = A::zero();
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc[w][c] = A::zero();
             const int row = r0 + warp + NW * w;
             ok[w] = row < nr;
             arow[w] = reinterpret_cast<const L*>(Am + int64_t(ok[w] ? row : 0) * kp);
         }
         int64_t ef = e0;                      // first segment not yet fully consumed
-        for (int c0 = 0; c0 < kp; c0 += C) {
-            const int cw = min(C, kp - c0);
+        for (int ch = 0; ch < kp; ch += C) {
+            const int cw = min(C, kp - ch);
             __syncthreads();
-            while (ef < e1 && seg_col[ef] + seg_len[ef] <= c0) ++ef;
+            while (ef < e1 && seg_col[ef] + seg_len[ef] <= ch) ++ef;
             for (int64_t e = ef; e < e1; ++e) {
                 const int sc = seg_col[e];
-                if (sc >= c0 + cw) break;
-                const int lo = max(sc, c0), hi = min(sc + seg_len[e], c0 + cw);
-                const V* src = vec + seg_off[e] + (lo - sc);
-                for (int j = threadIdx.x; j < hi - lo; j += blockDim.x) xs[lo - c0 + j] = src[j];
+                if (sc >= ch + cw) break;
+                const int lo = max(sc, ch), hi = min(sc + seg_len[e], ch + cw);
+                const V* src = vec + (seg_off[e] + (lo - sc)) * nrhs + c0;
+                const int n = (hi - lo) * NR;
+                for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                    const int rr = j / NR, cc = j - rr * NR;
+                    xs[(lo - ch + rr) * NR + cc] = src[int64_t(rr) * nrhs + cc];
+                }
             }
-            for (int j = max(ktot - c0, 0) + threadIdx.x; j < cw; j += blockDim.x) xs[j] = A::zero();
+            for (int j = max(ktot - ch, 0) * NR + threadIdx.x; j < cw * NR; j += blockDim.x)
+                xs[j] = A::zero();
             __syncthreads();
-            const int nv = cw / W, k0 = c0 / W;
-            // two k-steps per iteration: 2 * RW independent 16-byte loads per lane
+            const int nv = cw / W, k0 = ch / W;
             for (int k = lane; k < nv; k += 2 * kWarp) {
                 const bool two = k + kWarp < nv;
                 L a0[RW], a1[RW];
@@ -242,48 +260,62 @@ __global__ void __launch_bounds__(256) k_rowgemv(
                     if (ok[w]) a0[w] = __ldg(arow[w] + k0 + k);
                     if (ok[w] && two) a1[w] = __ldg(arow[w] + k0 + k + kWarp);
                 }
-                V x0[W], x1[W];
 #pragma unroll
                 for (int z = 0; z < W; ++z) {
-                    x0[z] = xs[k * W + z];
-                    x1[z] = two ? xs[(k + kWarp) * W + z] : A::zero();
-                }
+                    V x0[NR], x1[NR];
 #pragma unroll
-                for (int w = 0; w < RW; ++w)
-                    if (ok[w]) {
-#pragma unroll
-                        for (int z = 0; z < W; ++z) acc[w] = A::mac(acc[w], A::lget(a0[w], z), x0[z]);
-                        if (two) {
-#pragma unroll
-                            for (int z = 0; z < W; ++z) acc[w] = A::mac(acc[w], A::lget(a1[w], z), x1[z]);
-                        }
+                    for (int c = 0; c < NR; ++c) {
+                        x0[c] = xs[(k * W + z) * NR + c];
+                        x1[c] = two ? xs[((k + kWarp) * W + z) * NR + c] : A::zero();
                     }
+#pragma unroll
+                    for (int w = 0; w < RW; ++w)
+                        if (ok[w]) {
+                            const auto s0 = A::lget(a0[w], z);
+#pragma unroll
+                            for (int c = 0; c < NR; ++c) acc[w][c] = A::mac(acc[w][c], s0, x0[c]);
+                            if (two) {
+                                const auto s1 = A::lget(a1[w], z);
+#pragma unroll
+                                for (int c = 0; c < NR; ++c) acc[w][c] = A::mac(acc[w][c], s1, x1[c]);
+                            }
+                        }
+                }
             }
         }
 #pragma unroll
         for (int w = 0; w < RW; ++w) {
             if (!ok[w]) continue;
-            const V sum = warp_sum<A>(acc[w]);
             const int row = r0 + warp + NW * w;
-            if (lane == 0) y[row] = accumulate ? A::add(y[row], sum) : sum;
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                const V sum = warp_sum<A>(acc[w][c]);
+                if (lane == 0) {
+                    V* yo = y + int64_t(row) * nrhs + c;
+                    *yo = accumulate ? A::add(*yo, sum) : sum;
+                }
+            }
         }
     }
 }
 
 // ---- leaves, near field on the fly (F64 / F32) --------------------------------
-// phi_X = sum_b U_X^b u_X^b + sum_{X' in N(X)} K_{t^X, s^X'} q_X'; one CTA per
-// leaf, one target per thread; source points staged through shared memory.
-template <typename T, int D, int KIND>
+// phi_X = sum_b U_X^b u_X^b + sum_{X' in N(X)} K_{t^X, s^X'} q_X' for an NR-column
+// tile; one CTA per leaf, one target per thread; the kernel value of each pair
+// is evaluated once and applied to all NR columns; source points staged
+// through shared memory.
+template <typename T, int D, int KIND, int NR>
 __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t leaf_base,
                            const int64_t* __restrict__ leaf_ptr, const int64_t* __restrict__ near_ptr,
                            const int64_t* __restrict__ near_idx, const int32_t* __restrict__ rank,
                            const int64_t* __restrict__ voff, const int64_t* __restrict__ uoff,
                            const int32_t* __restrict__ ustride, const T* __restrict__ ops,
                            const T* __restrict__ u, const T* __restrict__ xs, int64_t N,
-                           const T* __restrict__ q, T* __restrict__ phi, T param, T diag) {
+                           const T* __restrict__ q, T* __restrict__ phi, T param, T diag,
+                           int nrhs, int c0) {
     constexpr int TILE = 128;
     __shared__ T sx[D][TILE];
-    __shared__ T sq[TILE];
+    __shared__ T sq[TILE * NR];
     const int64_t L = blockIdx.x;
     if (L >= nleaf) return;
     const int64_t p0 = leaf_ptr[L];
@@ -291,7 +323,9 @@ __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t lea
     for (int i0 = 0; i0 < m; i0 += blockDim.x) {
         const int i = i0 + threadIdx.x;
         const bool active = i < m;
-        T acc = T(0);
+        T acc[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] = T(0);
         T xi[D];
         if (active) {
 #pragma unroll
@@ -301,8 +335,12 @@ __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t lea
                 const int r = rank[s];
                 if (r == 0) continue;
                 const T* U = ops + uoff[s] + int64_t(i) * ustride[s];
-                const T* ub = u + voff[s];
-                for (int j = 0; j < r; ++j) acc += U[j] * ub[j];
+                const T* ub = u + voff[s] * nrhs + c0;
+                for (int j = 0; j < r; ++j) {
+                    const T a = U[j];
+#pragma unroll
+                    for (int c = 0; c < NR; ++c) acc[c] += a * ub[int64_t(j) * nrhs + c];
+                }
             }
         }
         for (int64_t e = near_ptr[L]; e < near_ptr[L + 1]; ++e) {
@@ -315,7 +353,8 @@ __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t lea
                 for (int j = threadIdx.x; j < nt; j += blockDim.x) {
 #pragma unroll
                     for (int k = 0; k < D; ++k) sx[k][j] = xs[k * N + s0 + j0 + j];
-                    sq[j] = q[s0 + j0 + j];
+#pragma unroll
+                    for (int c = 0; c < NR; ++c) sq[j * NR + c] = q[(s0 + j0 + j) * nrhs + c0 + c];
                 }
                 __syncthreads();
                 if (active) {
@@ -326,12 +365,17 @@ __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t lea
                             const T t = xi[k] - sx[k][j];
                             r2 = r2 + t * t;
                         }
-                        acc += kernel_r2<T, KIND>(r2, param, diag) * sq[j];
+                        const T g = kernel_r2<T, KIND>(r2, param, diag);
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) acc[c] += g * sq[j * NR + c];
                     }
                 }
             }
         }
-        if (active) phi[p0 + i] = acc;
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) phi[(p0 + i) * nrhs + c0 + c] = acc[c];
+        }
     }
 }
 
@@ -341,7 +385,7 @@ __global__ void k_lr_vtq(int64_t b0, int64_t nblk, const int64_t* __restrict__ y
                          const int64_t* __restrict__ my, const int32_t* __restrict__ kk,
                          const int64_t* __restrict__ voffs, const int64_t* __restrict__ toffs,
                          const T* __restrict__ ops, const T* __restrict__ q, T* __restrict__ t,
-                         int chunk) {
+                         int chunk, int nrhs, int col) {
     const int64_t blk = b0 + blockIdx.y;
     if (blockIdx.y >= nblk) return;
     const int64_t m = my[blk];
@@ -350,11 +394,12 @@ __global__ void k_lr_vtq(int64_t b0, int64_t nblk, const int64_t* __restrict__ y
     const int64_t i1 = min(m, i0 + chunk);
     const int k = kk[blk];
     const T* V = ops + voffs[blk];
-    const T* qy = q + y0[blk];
+    const T* qy = q + y0[blk] * nrhs;
     __shared__ T red[32];
     for (int c = 0; c < k; ++c) {
         T part = T(0);
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) part += V[c * m + i] * qy[i];
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+            part += V[c * m + i] * qy[i * nrhs + col];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if (threadIdx.x % kWarp == 0) red[threadIdx.x / kWarp] = part;
@@ -363,7 +408,7 @@ __global__ void k_lr_vtq(int64_t b0, int64_t nblk, const int64_t* __restrict__ y
             T s = threadIdx.x < blockDim.x / kWarp ? red[threadIdx.x] : T(0);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (threadIdx.x == 0) atomicAdd(t + toffs[blk] + c, s);
+            if (threadIdx.x == 0) atomicAdd(t + (toffs[blk] + c) * nrhs + col, s);
         }
         __syncthreads();
     }
@@ -375,7 +420,7 @@ __global__ void k_lr_ut(int64_t g0, int64_t ngroup, const int64_t* __restrict__ 
                         const int64_t* __restrict__ x0, const int64_t* __restrict__ mx,
                         const int32_t* __restrict__ kk, const int64_t* __restrict__ uoffs,
                         const int64_t* __restrict__ toffs, const T* __restrict__ ops,
-                        const T* __restrict__ t, T* __restrict__ phi) {
+                        const T* __restrict__ t, T* __restrict__ phi, int nrhs, int col) {
     const int64_t g = g0 + blockIdx.y;
     if (blockIdx.y >= ngroup) return;
     const int64_t bfirst = gptr[g], blast = gptr[g + 1];
@@ -386,10 +431,10 @@ __global__ void k_lr_ut(int64_t g0, int64_t ngroup, const int64_t* __restrict__ 
     for (int64_t blk = bfirst; blk < blast; ++blk) {
         const int k = kk[blk];
         const T* U = ops + uoffs[blk];
-        const T* tb = t + toffs[blk];
-        for (int c = 0; c < k; ++c) acc += U[c * m + i] * tb[c];
+        const T* tb = t + toffs[blk] * nrhs + col;
+        for (int c = 0; c < k; ++c) acc += U[c * m + i] * tb[int64_t(c) * nrhs];
     }
-    phi[x0[bfirst] + i] += acc;
+    phi[(x0[bfirst] + i) * nrhs + col] += acc;
 }
 
 }  // namespace h2
