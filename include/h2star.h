@@ -255,6 +255,48 @@ int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale, const dou
  */
 int h2_matvec_noalloc(h2_handle h, const double* x, double* y, void* stream);
 
+/* ---- batched products over many independent trees ------------------------ */
+typedef struct h2_batch_s* h2_batch;
+
+typedef struct {
+    int     instances, virtual_instances;   /* handles; (handle, RHS column) pairs      */
+    int64_t points_times_rhs;               /* sum over instances of N * nrhs          */
+    int64_t launches_per_product;           /* kernels in the captured product graph   */
+    int     m2m_steps, l2l_steps;           /* level-synchronous launch steps          */
+    int64_t m2l_tasks, leaf_tasks;          /* merged block-row tasks                  */
+    int64_t bytes_device, bytes_ops;        /* device memory; of it, operator entries  */
+} h2_batch_stats;
+
+/*
+ * h2_batch_create -- merge n handles (any mix of N, d, kernel and depth; one
+ * storage; stored near field, h2_build_opts.near_mode = 2; H2*(b+t) or
+ * H2_sqrt(d)(b)) into one device layout for batched products.  Handles may be
+ * host-only: their host representation is uploaded once more, into one operator
+ * array.  nrhs[i] in [1, 64] (NULL = all 1) is instance i's column count.
+ * Every (instance, column) pair becomes a virtual instance with its own
+ * coefficients; the tasks of all of them are merged so one product is ~2 kappa_max
+ * + 4 launches (P2M, M2M bottom-up and L2L top-down in level-synchronous steps,
+ * one M2L launch, one leaf launch, gather and scatter), captured once into a
+ * CUDA graph.  The handles may be destroyed afterwards.
+ * Errors: H2_E_INVALID_ARG, H2_E_UNSUPPORTED, H2_E_OOM, H2_E_CUDA.
+ */
+int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_batch* out);
+
+/*
+ * h2_batch_matvec -- Y[i] = K~_i X[i] for every instance i, replaying the graph.
+ * X[i], Y[i]: device, fp64, column-major N_i x nrhs[i] (leading dimension N_i),
+ * user point order; the host arrays X, Y of n pointers are read before the call
+ * returns.  Ordered after prior work on `stream`; later work on `stream` waits
+ * for it.  One product at a time per batch.  Errors: H2_E_INVALID_ARG, H2_E_CUDA.
+ */
+int h2_batch_matvec(h2_batch b, const double* const* X, double* const* Y, void* stream);
+
+/* h2_batch_info -- fill *st (host).  Errors: H2_E_INVALID_ARG. */
+int h2_batch_info(h2_batch b, h2_batch_stats* st);
+
+/* h2_batch_destroy -- release the batch (NULL is ignored); synchronises the device. */
+void h2_batch_destroy(h2_batch b);
+
 /* h2_last_error -- message of the last failure on this thread ("" if none). */
 const char* h2_last_error(void);
 

@@ -25,7 +25,8 @@ STORAGE = {"f64": 0, "f32": 1, "df64": 2}
 NEAR = {None: 0, "fly": 1, "stored": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
 EXPORTED = ("h2_build", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
-            "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy")
+            "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
+            "h2_batch_matvec", "h2_batch_info", "h2_batch_destroy")
 
 
 class BuildOpts(ctypes.Structure):
@@ -63,6 +64,14 @@ class GmresStats(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int), ("virtual_instances", ctypes.c_int),
+                ("points_times_rhs", ctypes.c_int64), ("launches_per_product", ctypes.c_int64),
+                ("m2m_steps", ctypes.c_int), ("l2l_steps", ctypes.c_int),
+                ("m2l_tasks", ctypes.c_int64), ("leaf_tasks", ctypes.c_int64),
+                ("bytes_device", ctypes.c_int64), ("bytes_ops", ctypes.c_int64)]
+
+
 class H2Error(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"h2 error {code}: {msg}")
@@ -92,11 +101,16 @@ def lib():
         L.h2_tree_order.argtypes = [c_vp, c_vp]
         L.h2_profile.argtypes = [c_vp, c_int]
         L.h2_stage_times.argtypes = [c_vp, c_vp, c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]
+        L.h2_batch_create.argtypes = [c_vp, c_int, c_vp, ctypes.POINTER(c_vp)]
+        L.h2_batch_matvec.argtypes = [c_vp, c_vp, c_vp, c_vp]
+        L.h2_batch_info.argtypes = [c_vp, ctypes.POINTER(BatchStats)]
+        L.h2_batch_destroy.argtypes = [c_vp]
+        L.h2_batch_destroy.restype = None
         L.h2_last_error.restype = ctypes.c_char_p
         L.h2_destroy.argtypes = [c_vp]
         L.h2_destroy.restype = None
         for name in EXPORTED:
-            if name not in ("h2_last_error", "h2_destroy"):
+            if name not in ("h2_last_error", "h2_destroy", "h2_batch_destroy"):
                 getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -238,3 +252,53 @@ class H2Matrix:
             self.close()
         except Exception:
             pass
+
+
+class H2Batch:
+    """Many independent compressed matrices applied together: one captured
+    CUDA graph of merged, level-synchronous launches per batched product."""
+
+    def __init__(self, matrices, nrhs=None):
+        self.matrices = list(matrices)
+        n = len(self.matrices)
+        self.nrhs = list(nrhs) if nrhs is not None else [1] * n
+        hs = (ctypes.c_void_p * n)(*[m._h.value for m in self.matrices])
+        nr = (ctypes.c_int * n)(*self.nrhs)
+        h = ctypes.c_void_p()
+        _check(lib().h2_batch_create(hs, n, nr, ctypes.byref(h)))
+        self._h = h
+
+    def info(self):
+        st = BatchStats()
+        _check(lib().h2_batch_info(self._h, ctypes.byref(st)))
+        return {f[0]: getattr(st, f[0]) for f in BatchStats._fields_}
+
+    def matvec(self, xs, outs=None, stream=None):
+        """xs[i]: float64 CUDA tensor (N_i,) or (N_i, nrhs_i); returns the products."""
+        import torch
+        n = len(self.matrices)
+        cols, outs2 = [], []
+        for i, (m, x) in enumerate(zip(self.matrices, xs)):
+            x2 = x.reshape(m.N, -1)
+            if x2.shape[1] != self.nrhs[i] or x2.dtype != torch.float64 or not x2.is_cuda:
+                raise ValueError(f"input {i} must be float64 CUDA with {self.nrhs[i]} columns")
+            cols.append(x2.t().contiguous())            # (nrhs, N): column c contiguous
+            outs2.append(torch.empty((self.nrhs[i], m.N), dtype=torch.float64, device=x.device)
+                         if outs is None else outs[i])
+        X = (ctypes.c_void_p * n)(*[c.data_ptr() for c in cols])
+        Y = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs2])
+        _check(lib().h2_batch_matvec(self._h, X, Y, _stream_ptr(stream)))
+        self._keep = (cols, outs2)
+        return [o.t() if self.nrhs[i] > 1 else o.reshape(-1) for i, o in enumerate(outs2)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().h2_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -200,8 +200,10 @@ void launch_rows_rw(const DevRowTasks& R, const void* ops, void* vec, cudaStream
         static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate, nrhs, c0);
 }
 
-// Largest RHS tile: 16 columns in fp32, 8 in fp64 / double-float.
-template <class A> constexpr int max_tile() { return std::is_same<A, h2::F32>::value ? 16 : 8; }
+// Largest RHS tile: 4 columns in fp32, 2 in fp64 / double-float.  Wider tiles
+// (8, 16) are compiled but lose: with fewer rows per warp every task re-stages
+// its coefficient tile once per 8 rows, so they are not used.
+template <class A> constexpr int max_tile() { return std::is_same<A, h2::F32>::value ? 4 : 2; }
 
 template <class A>
 void launch_rows(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate,
@@ -1073,5 +1075,357 @@ extern "C" int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale
     if (st) *st = S;
     if (!conv) return fail(H2_E_NOT_CONVERGED, "GMRES stopped at maxit before reaching rtol");
     return H2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched products over many independent trees: every (instance, RHS column)
+// is a virtual instance with its own coefficient regions; the task lists of
+// all of them are merged so that each MVP stage is one launch (M2M bottom-up
+// and L2L top-down in level-synchronous steps), and the whole sequence is
+// captured once into a CUDA graph and replayed.
+namespace {
+
+__global__ void k_batch_gather(int nv, const int64_t* __restrict__ pref, const int64_t* __restrict__ qb,
+                               const int64_t* __restrict__ pb, const int64_t* __restrict__ perm,
+                               const double* const* __restrict__ X, void* __restrict__ vec, int storage) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= pref[nv]) return;
+    int lo = 0, hi = nv;                       // vinst v with pref[v] <= t < pref[v + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (pref[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int64_t i = t - pref[lo];
+    const double x = X[lo][perm[pb[lo] + i]];
+    if (storage == H2_F64) static_cast<double*>(vec)[qb[lo] + i] = x;
+    else if (storage == H2_F32) static_cast<float*>(vec)[qb[lo] + i] = float(x);
+    else static_cast<float2*>(vec)[qb[lo] + i] = h2::DF::from_double(x);
+}
+
+__global__ void k_batch_scatter(int nv, const int64_t* __restrict__ pref, const int64_t* __restrict__ fb,
+                                const int64_t* __restrict__ pb, const int64_t* __restrict__ perm,
+                                double* const* __restrict__ Y, const void* __restrict__ vec, int storage) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= pref[nv]) return;
+    int lo = 0, hi = nv;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (pref[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int64_t i = t - pref[lo];
+    double y;
+    if (storage == H2_F64) y = static_cast<const double*>(vec)[fb[lo] + i];
+    else if (storage == H2_F32) y = double(static_cast<const float*>(vec)[fb[lo] + i]);
+    else y = h2::DF::to_double(static_cast<const float2*>(vec)[fb[lo] + i]);
+    Y[lo][perm[pb[lo] + i]] = y;
+}
+
+}  // namespace
+
+struct h2_batch_s {
+    int storage = 0, ninst = 0, nvirt = 0, device = -1;
+    size_t ssize = 8, vsize = 8;
+    std::vector<int> inst_of, col_of;          // per virtual instance
+    std::vector<int64_t> npts;                 // per virtual instance
+    int64_t total_pts = 0, veclen = 0, ops_len = 0;
+    void* ops = nullptr;
+    void* vec = nullptr;
+    int64_t* perm = nullptr;                   // concatenated per instance
+    int64_t *pref = nullptr, *qb = nullptr, *fb = nullptr, *pb = nullptr;
+    const double** Xtab = nullptr;             // device tables of user pointers
+    double** Ytab = nullptr;
+    int64_t u_begin = 0, u_len = 0, phi_begin = 0, phi_len = 0;
+    DevRowTasks p2m, m2l, leaf;
+    std::vector<DevRowTasks> m2m, l2l;         // level-synchronous steps
+    int64_t launches = 0;                      // kernels per batched MVP
+    std::vector<void*> allocs;
+    int64_t bytes_device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~h2_batch_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (stream) cudaStreamDestroy(stream);
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+template <typename U>
+int bupload(h2_batch b, U** dst, const std::vector<U>& src) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(src.size(), 1) * sizeof(U));
+    if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    b->allocs.push_back(p);
+    b->bytes_device += int64_t(std::max<size_t>(src.size(), 1) * sizeof(U));
+    if (!src.empty()) H2_CUDA(cudaMemcpy(p, src.data(), src.size() * sizeof(U), cudaMemcpyHostToDevice));
+    *dst = static_cast<U*>(p);
+    return H2_OK;
+}
+
+int bupload_rows(h2_batch b, DevRowTasks& D, const h2::RowTasks& R) {
+    D.n = R.size();
+    H2_TRY(bupload(b, &D.dst, R.dst));
+    H2_TRY(bupload(b, &D.aoff, R.aoff));
+    H2_TRY(bupload(b, &D.seg_ptr, R.seg_ptr));
+    H2_TRY(bupload(b, &D.seg_off, R.seg_off));
+    H2_TRY(bupload(b, &D.rows, R.rows));
+    H2_TRY(bupload(b, &D.kpad, R.kpad));
+    H2_TRY(bupload(b, &D.seg_len, R.seg_len));
+    H2_TRY(bupload(b, &D.seg_col, R.seg_col));
+    D.rw = 4;
+    return H2_OK;
+}
+
+// Append the tasks of R (one instance's layout) to M with ops offset abase and
+// coefficient offsets remapped by `map`.
+template <class F>
+void append_rows(h2::RowTasks& M, const h2::RowTasks& R, int64_t abase, F map) {
+    for (int64_t k = 0; k < R.size(); ++k) {
+        M.add(map(R.dst[k]), R.rows[k], R.kpad[k], abase + R.aoff[k]);
+        for (int64_t e = R.seg_ptr[k]; e < R.seg_ptr[k + 1]; ++e) M.seg(map(R.seg_off[e]), R.seg_len[e]);
+        M.close();
+    }
+}
+
+template <class A>
+int batch_launch_all(h2_batch b, cudaStream_t s) {
+    using V = typename A::V;
+    b->launches = 0;
+    const int threads = 256;
+    ++b->launches;
+    k_batch_gather<<<nblocks(b->total_pts, threads), threads, 0, s>>>(
+        b->nvirt, b->pref, b->qb, b->pb, b->perm, b->Xtab, b->vec, b->storage);
+    auto rows = [&](const DevRowTasks& R, int acc) {
+        if (R.n == 0) return;
+        ++b->launches;
+        launch_rows<A>(R, b->ops, b->vec, s, acc);
+    };
+    rows(b->p2m, 0);
+    for (const auto& R : b->m2m) rows(R, 0);
+    V* vec = static_cast<V*>(b->vec);
+    if (b->u_len > 0) cudaMemsetAsync(vec + b->u_begin, 0, sizeof(V) * b->u_len, s);
+    rows(b->m2l, 0);
+    for (const auto& R : b->l2l) rows(R, 1);
+    if (b->phi_len > 0) cudaMemsetAsync(vec + b->phi_begin, 0, sizeof(V) * b->phi_len, s);
+    rows(b->leaf, 0);
+    ++b->launches;
+    k_batch_scatter<<<nblocks(b->total_pts, threads), threads, 0, s>>>(
+        b->nvirt, b->pref, b->fb, b->pb, b->perm, b->Ytab, b->vec, b->storage);
+    return H2_OK;
+}
+
+}  // namespace
+
+extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_batch* out) {
+    g_err.clear();
+    if (!hs || !out || n < 1) return fail(H2_E_INVALID_ARG, "NULL argument or n < 1");
+    *out = nullptr;
+    const int storage = hs[0] ? hs[0]->host.storage : -1;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return fail(H2_E_INVALID_ARG, "NULL handle in the batch");
+        if (hs[i]->host.storage != storage) return fail(H2_E_INVALID_ARG, "handles differ in storage");
+        if (!hs[i]->host.packed.near_stored)
+            return fail(H2_E_UNSUPPORTED, "batched products need the stored near field (near_mode 2)");
+        if (hs[i]->host.variant == H2_PLUS_H_STAR)
+            return fail(H2_E_UNSUPPORTED, "batched products support H2*(b+t) and H2_sqrt(d)(b)");
+        const int r = nrhs ? nrhs[i] : 1;
+        if (r < 1 || r > 64) return fail(H2_E_INVALID_ARG, "nrhs must be in [1, 64]");
+    }
+    std::unique_ptr<h2_batch_s> B(new h2_batch_s());
+    B->storage = storage;
+    B->ninst = n;
+    B->ssize = storage == H2_F32 ? 4 : 8;
+    B->vsize = B->ssize;
+    H2_CUDA(cudaGetDevice(&B->device));
+    // ops: instances back to back (each block already 4-aligned inside its instance)
+    std::vector<int64_t> abase(n);
+    int64_t ol = 0;
+    for (int i = 0; i < n; ++i) {
+        abase[i] = ol;
+        ol += (int64_t(hs[i]->host.packed.ops.size()) + 3) / 4 * 4;
+    }
+    B->ops_len = ol;
+    // virtual instances and the coefficient layout [Q | V | U | PHI]
+    int64_t totN = 0, totV = 0;
+    std::vector<int64_t> qoff, voff, pbase(n);
+    int64_t pb = 0;
+    for (int i = 0; i < n; ++i) {
+        pbase[i] = pb;
+        pb += hs[i]->host.tree.N;
+        for (int c = 0; c < (nrhs ? nrhs[i] : 1); ++c) {
+            B->inst_of.push_back(i);
+            B->col_of.push_back(c);
+            B->npts.push_back(hs[i]->host.tree.N);
+            qoff.push_back(totN);
+            voff.push_back(totV);
+            totN += hs[i]->host.tree.N;
+            totV += hs[i]->host.packed.vlen;
+        }
+    }
+    B->nvirt = int(B->inst_of.size());
+    B->total_pts = totN;
+    const int64_t Qb = 0, Vb = totN, Ub = totN + totV, Fb = totN + 2 * totV;
+    B->veclen = 2 * totN + 2 * totV;
+    B->u_begin = Ub;
+    B->u_len = totV;
+    B->phi_begin = Fb;
+    B->phi_len = totN;
+    h2::RowTasks p2m, m2l, leaf;
+    int kmax = 0;
+    for (int i = 0; i < n; ++i) kmax = std::max(kmax, hs[i]->host.tree.kappa);
+    std::vector<h2::RowTasks> m2m(std::max(kmax, 1)), l2l(kmax + 1);
+    for (int v = 0; v < B->nvirt; ++v) {
+        const h2::Host& H = hs[B->inst_of[v]]->host;
+        const h2::Packed& P = H.packed;
+        const int64_t N = H.tree.N, vlen = P.vlen;
+        auto map = [&](int64_t o) -> int64_t {
+            if (o < N) return Qb + qoff[v] + o;
+            if (o < N + vlen) return Vb + voff[v] + (o - N);
+            if (o < N + 2 * vlen) return Ub + voff[v] + (o - N - vlen);
+            return Fb + qoff[v] + (o - N - 2 * vlen);
+        };
+        const int64_t ab = abase[B->inst_of[v]];
+        append_rows(p2m, P.p2m, ab, map);
+        append_rows(m2l, P.m2l, ab, map);
+        append_rows(leaf, P.leaf, ab, map);
+        const int K = H.tree.kappa;
+        for (int l = K - 1; l >= 1; --l) append_rows(m2m[K - 1 - l], P.m2m[l], ab, map);   // bottom-up
+        for (int l = 2; l <= K; ++l) append_rows(l2l[l], P.l2l[l], ab, map);              // top-down
+    }
+    // device data
+    {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(size_t(ol), 1) * B->ssize);
+        if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        B->allocs.push_back(p);
+        B->bytes_device += int64_t(ol) * int64_t(B->ssize);
+        B->ops = p;
+        const size_t chunk = size_t(1) << 24;
+        for (int i = 0; i < n; ++i) {
+            const std::vector<double>& src = hs[i]->host.packed.ops;
+            for (size_t o = 0; o < src.size(); o += chunk) {
+                const size_t c = std::min(chunk, src.size() - o);
+                if (storage == H2_F64) {
+                    H2_CUDA(cudaMemcpy(static_cast<double*>(p) + abase[i] + o, src.data() + o, c * 8,
+                                       cudaMemcpyHostToDevice));
+                } else if (storage == H2_F32) {
+                    std::vector<float> buf(c);
+                    for (size_t k = 0; k < c; ++k) buf[k] = float(src[o + k]);
+                    H2_CUDA(cudaMemcpy(static_cast<float*>(p) + abase[i] + o, buf.data(), c * 4,
+                                       cudaMemcpyHostToDevice));
+                } else {
+                    std::vector<float2> buf(c);
+                    for (size_t k = 0; k < c; ++k) buf[k] = Conv<h2::DF>::of(src[o + k]);
+                    H2_CUDA(cudaMemcpy(static_cast<float2*>(p) + abase[i] + o, buf.data(), c * 8,
+                                       cudaMemcpyHostToDevice));
+                }
+            }
+        }
+        e = cudaMalloc(&p, std::max<size_t>(size_t(B->veclen), 1) * B->vsize);
+        if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        B->allocs.push_back(p);
+        B->bytes_device += int64_t(B->veclen) * int64_t(B->vsize);
+        B->vec = p;
+    }
+    std::vector<int64_t> perm;
+    for (int i = 0; i < n; ++i) perm.insert(perm.end(), hs[i]->host.tree.perm.begin(), hs[i]->host.tree.perm.end());
+    std::vector<int64_t> pref(B->nvirt + 1, 0), qbv(B->nvirt), fbv(B->nvirt), pbv(B->nvirt);
+    for (int v = 0; v < B->nvirt; ++v) {
+        pref[v + 1] = pref[v] + B->npts[v];
+        qbv[v] = Qb + qoff[v];
+        fbv[v] = Fb + qoff[v];
+        pbv[v] = pbase[B->inst_of[v]];
+    }
+    H2_TRY(bupload(B.get(), &B->perm, perm));
+    H2_TRY(bupload(B.get(), &B->pref, pref));
+    H2_TRY(bupload(B.get(), &B->qb, qbv));
+    H2_TRY(bupload(B.get(), &B->fb, fbv));
+    H2_TRY(bupload(B.get(), &B->pb, pbv));
+    std::vector<const double*> nullx(B->nvirt, nullptr);
+    std::vector<double*> nully(B->nvirt, nullptr);
+    H2_TRY(bupload(B.get(), &B->Xtab, nullx));
+    H2_TRY(bupload(B.get(), &B->Ytab, nully));
+    H2_TRY(bupload_rows(B.get(), B->p2m, p2m));
+    H2_TRY(bupload_rows(B.get(), B->m2l, m2l));
+    H2_TRY(bupload_rows(B.get(), B->leaf, leaf));
+    for (auto& R : m2m) {
+        if (R.size() == 0) continue;
+        B->m2m.emplace_back();
+        H2_TRY(bupload_rows(B.get(), B->m2m.back(), R));
+    }
+    for (auto& R : l2l) {
+        if (R.size() == 0) continue;
+        B->l2l.emplace_back();
+        H2_TRY(bupload_rows(B.get(), B->l2l.back(), R));
+    }
+    H2_CUDA(cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking));
+    H2_CUDA(cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming));
+    H2_CUDA(cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming));
+    // capture the whole batched product once
+    H2_CUDA(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = (storage == H2_F64)   ? batch_launch_all<h2::F64>(B.get(), B->stream)
+             : (storage == H2_F32) ? batch_launch_all<h2::F32>(B.get(), B->stream)
+                                   : batch_launch_all<h2::DF>(B.get(), B->stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B->stream, &g);
+    if (rc != H2_OK) return rc;
+    if (e != cudaSuccess) return fail(H2_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    B->graph = g;
+    H2_CUDA(cudaGraphInstantiate(&B->exec, g, 0));
+    *out = B.release();
+    return H2_OK;
+}
+
+extern "C" int h2_batch_matvec(h2_batch b, const double* const* X, double* const* Y, void* stream) {
+    g_err.clear();
+    if (!b || !X || !Y) return fail(H2_E_INVALID_ARG, "NULL argument");
+    // per virtual instance: column c of instance i at X[i] + c * N_i (column-major, ld = N_i)
+    std::vector<const double*> xt(b->nvirt);
+    std::vector<double*> yt(b->nvirt);
+    for (int v = 0; v < b->nvirt; ++v) {
+        const int i = b->inst_of[v];
+        if (!X[i] || !Y[i]) return fail(H2_E_INVALID_ARG, "NULL input or output pointer");
+        xt[v] = X[i] + int64_t(b->col_of[v]) * b->npts[v];
+        yt[v] = Y[i] + int64_t(b->col_of[v]) * b->npts[v];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    H2_CUDA(cudaEventRecord(b->ev_in, s));
+    H2_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    // pageable source: the copies are staged before the calls return
+    H2_CUDA(cudaMemcpyAsync(b->Xtab, xt.data(), sizeof(void*) * b->nvirt, cudaMemcpyHostToDevice, b->stream));
+    H2_CUDA(cudaMemcpyAsync(b->Ytab, yt.data(), sizeof(void*) * b->nvirt, cudaMemcpyHostToDevice, b->stream));
+    H2_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    H2_CUDA(cudaEventRecord(b->ev_out, b->stream));
+    H2_CUDA(cudaStreamWaitEvent(s, b->ev_out, 0));
+    return H2_OK;
+}
+
+extern "C" int h2_batch_info(h2_batch b, h2_batch_stats* st) {
+    g_err.clear();
+    if (!b || !st) return fail(H2_E_INVALID_ARG, "NULL argument");
+    std::memset(st, 0, sizeof(*st));
+    st->instances = b->ninst;
+    st->virtual_instances = b->nvirt;
+    st->points_times_rhs = b->total_pts;
+    st->launches_per_product = b->launches;
+    st->m2m_steps = int(b->m2m.size());
+    st->l2l_steps = int(b->l2l.size());
+    st->m2l_tasks = b->m2l.n;
+    st->leaf_tasks = b->leaf.n;
+    st->bytes_device = b->bytes_device;
+    st->bytes_ops = b->ops_len * int64_t(b->ssize);
+    return H2_OK;
+}
+
+extern "C" void h2_batch_destroy(h2_batch b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    delete b;   // the destructor releases the graph, stream, events and memory
 }
 
