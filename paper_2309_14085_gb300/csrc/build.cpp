@@ -231,7 +231,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
     std::vector<std::vector<double>>& us = out.us;
     std::vector<std::vector<double>>& vs = out.vs;
     std::vector<char> row_used(nI, 0), col_used(nJ, 0);
-    std::vector<double> r(nJ), u(nI);
+    std::vector<double> r(nJ), rn(nJ), u(nI), pv;
     double S2 = 0.0;
     int64_t i = 0;
     const int64_t kmax = std::min(nI, nJ);
@@ -240,13 +240,17 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
             if (!row_used[a]) return a;
         return -1;
     };
-    while (int64_t(out.rows.size()) < kmax) {
-        for (int64_t j = 0; j < nJ; ++j) r[j] = entry(i, j);
+    // residual row of row position `ir` against every accepted cross, l in order
+    auto fresh_row = [&](int64_t ir, std::vector<double>& out_r) {
+        for (int64_t j = 0; j < nJ; ++j) out_r[j] = entry(ir, j);
         for (size_t l = 0; l < us.size(); ++l) {
-            const double a = us[l][i];
+            const double a = us[l][ir];
             const double* vl = vs[l].data();
-            for (int64_t j = 0; j < nJ; ++j) r[j] = r[j] - a * vl[j];
+            for (int64_t j = 0; j < nJ; ++j) out_r[j] = out_r[j] - a * vl[j];
         }
+    };
+    fresh_row(i, r);
+    while (int64_t(out.rows.size()) < kmax) {
         row_used[i] = 1;
         int64_t jb = -1;
         double best = -1.0;
@@ -257,6 +261,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         if (best <= 0.0) {
             i = next_free_row();
             if (i < 0) break;
+            fresh_row(i, r);
             continue;
         }
         const double piv = r[jb];
@@ -264,37 +269,67 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         for (int64_t j = 0; j < nJ; ++j) v[j] = r[j] / piv;
         for (int64_t a = 0; a < nI; ++a) u[a] = entry(a, jb);
         for (size_t l = 0; l < us.size(); ++l) {
-            const double b = vs[l][jb];
+            const double bb = vs[l][jb];
             const double* ul = us[l].data();
-            for (int64_t a = 0; a < nI; ++a) u[a] = u[a] - b * ul[a];
+            for (int64_t a = 0; a < nI; ++a) u[a] = u[a] - bb * ul[a];
         }
         col_used[jb] = 1;
-        double uu = 0.0, vv = 0.0, cross = 0.0;
+        double uu = 0.0, vv = 0.0;
         for (int64_t a = 0; a < nI; ++a) uu += u[a] * u[a];
         for (int64_t j = 0; j < nJ; ++j) vv += v[j] * v[j];
+        // next row: first argmax of |u| over unused rows (the same choice the
+        // step after the stopping test makes)
+        int64_t ib = -1;
+        double bi = -1.0;
+        for (int64_t a = 0; a < nI; ++a) {
+            const double q = row_used[a] ? -1.0 : std::fabs(u[a]);
+            if (q > bi) { bi = q; ib = a; }
+        }
+        const bool fuse = bi > 0.0;
+        // one pass over the previous crosses: v_l . v for the norm update and,
+        // when the next row is known, its residual (same order of operations
+        // as computing them separately)
+        pv.assign(us.size(), 0.0);
+        if (fuse)
+            for (int64_t j = 0; j < nJ; ++j) rn[j] = entry(ib, j);
         for (size_t l = 0; l < us.size(); ++l) {
-            double pu = 0.0, pv = 0.0;
-            for (int64_t a = 0; a < nI; ++a) pu += us[l][a] * u[a];
-            for (int64_t j = 0; j < nJ; ++j) pv += vs[l][j] * v[j];
-            cross += pu * pv;
+            const double* vl = vs[l].data();
+            double s = 0.0;
+            if (fuse) {
+                const double a = us[l][ib];
+                for (int64_t j = 0; j < nJ; ++j) {
+                    rn[j] = rn[j] - a * vl[j];
+                    s += vl[j] * v[j];
+                }
+            } else {
+                for (int64_t j = 0; j < nJ; ++j) s += vl[j] * v[j];
+            }
+            pv[l] = s;
+        }
+        double cross = 0.0;
+        for (size_t l = 0; l < us.size(); ++l) {
+            double pu = 0.0;
+            const double* ul = us[l].data();
+            for (int64_t a = 0; a < nI; ++a) pu += ul[a] * u[a];
+            cross += pu * pv[l];
         }
         S2 = S2 + 2.0 * cross + uu * vv;
+        if (fuse) {
+            const double a = u[ib];
+            for (int64_t j = 0; j < nJ; ++j) rn[j] = rn[j] - a * v[j];
+        }
         us.emplace_back(u);
         vs.emplace_back(std::move(v));
         out.rows.push_back(int(i));
         out.cols.push_back(int(jb));
         if (std::sqrt(uu) * std::sqrt(vv) <= eps * std::sqrt(std::max(S2, 0.0))) break;
-        int64_t ib = -1;
-        best = -1.0;
-        for (int64_t a = 0; a < nI; ++a) {
-            const double q = row_used[a] ? -1.0 : std::fabs(u[a]);
-            if (q > best) { best = q; ib = a; }
-        }
-        if (best <= 0.0) {
+        if (fuse) {
+            i = ib;
+            std::swap(r, rn);
+        } else {
             i = next_free_row();
             if (i < 0) break;
-        } else {
-            i = ib;
+            fresh_row(i, r);
         }
     }
     if (!keep) {

@@ -45,3 +45,21 @@ def workload(name):
     w["points"] = points(w["N"], w["d"], 1000 + w["number"])
     w["q"] = rhs(w["N"], w["nrhs"], 2000 + w["number"])
     return w
+
+
+def batched_instances(count=512, seed0=3000):
+    """The batched workload: instance k has N = floor(exp(U[ln 1024, ln 65536]))
+    points uniform in the unit square (k even, log r) or cube (k odd, 1/r),
+    1 + (k mod 16) right-hand sides N(0, 1); all streams seeded with 3000 + k."""
+    out = []
+    for k in range(count):
+        rng = np.random.Generator(np.random.PCG64(seed0 + k))
+        N = int(np.floor(np.exp(rng.uniform(np.log(1024), np.log(65536)))))
+        d = 2 if k % 2 == 0 else 3
+        P = rng.uniform(0.0, 1.0, size=(N, d))
+        r = 1 + (k % 16)
+        q = rng.standard_normal(size=(r, N)).T.copy()
+        out.append(dict(k=k, N=N, d=d, kernel="log2d" if d == 2 else "invr", points=P, q=q,
+                        nrhs=r))
+    return out
+
