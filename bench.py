@@ -318,6 +318,65 @@ def bench_gmres(handles, w, nsolve=10, rtol=1e-8):
     return out
 
 
+def bench_batched(args):
+    """Batched uneven instances: the first --instances of the 512-instance
+    workload (N log-uniform in [1024, 65536], 2D log r / 3D 1/r alternating,
+    1 + (k mod 16) RHS, eps 1e-8, fp32, stored near field), one H2Batch."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    from paper_2309_14085_gb300 import H2Batch, H2Matrix, inputs
+    inst = inputs.batched_instances(args.instances)
+    t0 = time.perf_counter()
+    ncpu = os.cpu_count() or 8
+
+    def build(i):
+        # large instances get more host threads
+        th = max(1, min(ncpu, int(ncpu * i["N"] / 65536.0) or 1))
+        return H2Matrix(i["points"], i["kernel"], leaf_size=64, tol=1e-8, storage=args.storage,
+                        near="stored", host_only=True, threads=th)
+
+    order = sorted(range(len(inst)), key=lambda k: -inst[k]["N"])
+    mats = [None] * len(inst)
+    with ThreadPoolExecutor(max(1, ncpu // 2)) as ex:
+        for k, m in zip(order, ex.map(build, [inst[k] for k in order])):
+            mats[k] = m
+    build_s = time.perf_counter() - t0
+    B = H2Batch(mats, [i["nrhs"] for i in inst])
+    info = B.info()
+    for m in mats:
+        m.close()
+    xs = [torch.tensor(i["q"], device="cuda") for i in inst]
+    for _ in range(args.warmup):
+        B.matvec(xs)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        B.matvec(xs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    pts = info["points_times_rhs"]
+    out = {"metric": METRIC, "value": pts / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+           "config": {"workload": f"c4_batched ({args.instances} of 512 instances)",
+                      "instances": args.instances, "points_times_rhs": pts,
+                      "launches_per_product": info["launches_per_product"],
+                      "graph": "one captured CUDA graph per batched product",
+                      "host_build_seconds": round(build_s, 1),
+                      "device_bytes": info["bytes_device"], "l2": "operators larger than L2"},
+           "clocks": clk, "gpu_launches": info["launches_per_product"] * args.steps}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,6 +392,7 @@ def main():
     ap.add_argument("--also", default="df64,f32",
                     help="other storage modes measured in the same run (comma list, '' for none)")
     ap.add_argument("--oracle-child", nargs=2, default=None)
+    ap.add_argument("--instances", type=int, default=64, help="batched workload: instance count")
     args = ap.parse_args()
     if args.oracle_child:
         oracle_rows_child(args.oracle_child[0], float(args.oracle_child[1]))
@@ -340,6 +400,12 @@ def main():
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+
+    if args.workload == "c4_batched":
+        if args.storage == "f64" and "--storage" not in sys.argv:
+            args.storage = "f32"
+        bench_batched(args)
+        return
 
     if args.impl == "reference":
         if rank != 0:

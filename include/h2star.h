@@ -297,6 +297,70 @@ int h2_batch_info(h2_batch b, h2_batch_stats* st);
 /* h2_batch_destroy -- release the batch (NULL is ignored); synchronises the device. */
 void h2_batch_destroy(h2_batch b);
 
+/* ---- served solves: a continuous-batching GMRES server --------------------- */
+typedef struct h2_server_s* h2_server;
+
+typedef struct {
+    int64_t workspace_bytes;   /* device budget for request workspaces (admission by HBM
+                                  footprint); 0 = max_active requests of the largest N  */
+    int     restart;           /* GMRES(restart) per request (default 50)               */
+    int     max_active;        /* requests iterated together at most (default 16)       */
+} h2_server_opts;
+
+typedef struct {
+    int64_t submitted, admitted, completed, queued, active, max_active;
+    int64_t ticks;             /* GMRES steps of the whole active set                  */
+    int64_t products;          /* multi-RHS products (one per geometry per tick)       */
+    int64_t product_columns;   /* request vectors those products carried               */
+    int64_t workspace_bytes;
+} h2_server_stats;
+
+typedef struct {
+    int    converged, iterations, restarts;
+    double rel_residual;       /* ||f - A x|| / ||f||, recomputed at the end            */
+    double queue_seconds;      /* submit -> admission                                   */
+    double latency_seconds;    /* submit -> solution ready                              */
+} h2_request_stats;
+
+/*
+ * h2_server_create -- start a solve server over resident geometries (handles
+ * built by h2_build on the current device; they stay owned by the caller and
+ * must outlive the server; each is used by the server only).  One worker
+ * thread iterates all admitted requests together: each tick performs one
+ * GMRES step (fp64 vectors, classical Gram-Schmidt twice) for every active
+ * request, the products of the requests on one geometry running as a single
+ * multi-RHS h2 product and different geometries on their own CUDA streams, so
+ * their work overlaps on the device.  Requests that arrive while others run
+ * join at the next tick once their Krylov workspace ((restart + 1 + 3) N
+ * doubles) fits the budget and a slot is free (first come, first served).
+ * Errors: H2_E_INVALID_ARG, H2_E_OOM, H2_E_CUDA.
+ */
+int h2_server_create(const h2_handle* geoms, int ngeom, const h2_server_opts* opts, h2_server* out);
+
+/*
+ * h2_server_submit -- queue a solve of (shift I + scale K~_geom) x = f to relative
+ * residual rtol within maxit iterations.  f: host, N fp64 in user order, copied
+ * before the call returns.  *ticket identifies the request.  Non-blocking.
+ * Errors: H2_E_INVALID_ARG, H2_E_OOM (workspace larger than the whole budget),
+ * H2_E_CUDA (the server stopped after a device error).
+ */
+int h2_server_submit(h2_server s, int geom, double shift, double scale, const double* f,
+                     double rtol, int maxit, int64_t* ticket);
+
+/*
+ * h2_server_wait -- block until the request is done; x (host, N, nullable)
+ * receives the solution and st (nullable) its statistics.  Each ticket is
+ * waited for once.  Returns H2_E_NOT_CONVERGED (x and st still filled) when
+ * maxit ran out.  Errors: H2_E_INVALID_ARG (unknown ticket).
+ */
+int h2_server_wait(h2_server s, int64_t ticket, double* x, h2_request_stats* st);
+
+/* h2_server_stats_get -- counters of the server (host).  Errors: H2_E_INVALID_ARG. */
+int h2_server_stats_get(h2_server s, h2_server_stats* st);
+
+/* h2_server_destroy -- drop queued requests, finish the active ones, stop the worker. */
+void h2_server_destroy(h2_server s);
+
 /* h2_last_error -- message of the last failure on this thread ("" if none). */
 const char* h2_last_error(void);
 

@@ -26,7 +26,8 @@ NEAR = {None: 0, "fly": 1, "stored": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
 EXPORTED = ("h2_build", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
-            "h2_batch_matvec", "h2_batch_info", "h2_batch_destroy")
+            "h2_batch_matvec", "h2_batch_info", "h2_batch_destroy", "h2_server_create",
+            "h2_server_submit", "h2_server_wait", "h2_server_stats_get", "h2_server_destroy")
 
 
 class BuildOpts(ctypes.Structure):
@@ -72,6 +73,23 @@ class BatchStats(ctypes.Structure):
                 ("bytes_device", ctypes.c_int64), ("bytes_ops", ctypes.c_int64)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("workspace_bytes", ctypes.c_int64), ("restart", ctypes.c_int),
+                ("max_active", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "submitted", "admitted", "completed", "queued", "active", "max_active", "ticks",
+        "products", "product_columns", "workspace_bytes")]
+
+
+class RequestStats(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("queue_seconds", ctypes.c_double), ("latency_seconds", ctypes.c_double)]
+
+
 class H2Error(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"h2 error {code}: {msg}")
@@ -106,11 +124,18 @@ def lib():
         L.h2_batch_info.argtypes = [c_vp, ctypes.POINTER(BatchStats)]
         L.h2_batch_destroy.argtypes = [c_vp]
         L.h2_batch_destroy.restype = None
+        L.h2_server_create.argtypes = [c_vp, c_int, ctypes.POINTER(ServerOpts), ctypes.POINTER(c_vp)]
+        L.h2_server_submit.argtypes = [c_vp, c_int, c_dbl, c_dbl, c_vp, c_dbl, c_int,
+                                       ctypes.POINTER(c_i64)]
+        L.h2_server_wait.argtypes = [c_vp, c_i64, c_vp, ctypes.POINTER(RequestStats)]
+        L.h2_server_stats_get.argtypes = [c_vp, ctypes.POINTER(ServerStats)]
+        L.h2_server_destroy.argtypes = [c_vp]
+        L.h2_server_destroy.restype = None
         L.h2_last_error.restype = ctypes.c_char_p
         L.h2_destroy.argtypes = [c_vp]
         L.h2_destroy.restype = None
         for name in EXPORTED:
-            if name not in ("h2_last_error", "h2_destroy", "h2_batch_destroy"):
+            if name not in ("h2_last_error", "h2_destroy", "h2_batch_destroy", "h2_server_destroy"):
                 getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -294,6 +319,55 @@ class H2Batch:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().h2_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class H2Server:
+    """Continuous-batching solve server over resident geometries (H2Matrix on
+    the device).  submit() queues a solve and returns at once; wait() blocks
+    for its solution; requests that arrive while others run join the active
+    set as workspace frees up."""
+
+    def __init__(self, geometries, workspace_bytes=0, restart=50, max_active=16):
+        self.geometries = list(geometries)
+        n = len(self.geometries)
+        hs = (ctypes.c_void_p * n)(*[g._h.value for g in self.geometries])
+        o = ServerOpts(workspace_bytes, restart, max_active)
+        h = ctypes.c_void_p()
+        _check(lib().h2_server_create(hs, n, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, geom, f, shift=0.0, scale=1.0, rtol=1e-8, maxit=1000):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        t = ctypes.c_int64()
+        _check(lib().h2_server_submit(self._h, geom, shift, scale, f.ctypes.data, rtol, maxit,
+                                      ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket):
+        """(x, stats) of a submitted request; stats["converged"] tells whether rtol was met."""
+        # the ticket's geometry is not tracked here: the library copies N values
+        st = RequestStats()
+        x = np.zeros(max(g.N for g in self.geometries))
+        rc = lib().h2_server_wait(self._h, ticket, x.ctypes.data, ctypes.byref(st))
+        if rc not in (0, -4):
+            _check(rc)
+        return x, {f[0]: getattr(st, f[0]) for f in RequestStats._fields_}
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().h2_server_stats_get(self._h, ctypes.byref(st)))
+        return {f[0]: getattr(st, f[0]) for f in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().h2_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

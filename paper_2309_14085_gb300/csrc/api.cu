@@ -9,8 +9,13 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -195,9 +200,9 @@ int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize
 template <class A, int RW, int NR>
 void launch_rows_rw(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate,
                     int nrhs, int c0) {
-    h2::k_rowgemv<A, RW, NR><<<unsigned(R.n), 256, 0, s>>>(
-        R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
-        static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate, nrhs, c0);
+    h2::k_rowgemv<A, RW, NR, false><<<unsigned(R.n), 256, 0, s>>>(
+            R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
+            static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate, nrhs, c0);
 }
 
 // Largest RHS tile: 4 columns in fp32, 2 in fp64 / double-float.  Wider tiles
@@ -239,35 +244,42 @@ std::vector<std::pair<int, int>> rhs_tiles(int nrhs) {
 
 // Autotuner: for the two large block-row lists (M2L and the stored leaf rows)
 // time 2, 4 and 8 rows per warp on the device (the coefficient buffer is
-// scratch here) and keep the fastest.  Small lists use 4.
+// scratch here): the fastest of 5 individually timed launches per width; 4
+// rows stays unless another width is more than 3 % faster.  Small lists use 4.
 template <class A>
 int autotune(h2_handle h) {
-    cudaEvent_t e0, e1;
-    H2_CUDA(cudaEventCreate(&e0));
-    H2_CUDA(cudaEventCreate(&e1));
+    cudaEvent_t ev[6];
+    for (auto& e : ev) H2_CUDA(cudaEventCreate(&e));
     DevRowTasks* lists[2] = {&h->m2l, &h->leaf};
     const int rws[3] = {2, 4, 8};
     for (int li = 0; li < 2; ++li) {
         DevRowTasks& R = *lists[li];
         if (R.n == 0) continue;
-        double best = 1e30;
-        int best_rw = 4;
+        double t[3];
         for (int k = 0; k < 3; ++k) {
             R.rw = rws[k];
             launch_rows<A>(R, h->ops, h->vec, 0, 0);          // warm-up
-            H2_CUDA(cudaEventRecord(e0, 0));
-            for (int it = 0; it < 3; ++it) launch_rows<A>(R, h->ops, h->vec, 0, 0);
-            H2_CUDA(cudaEventRecord(e1, 0));
-            H2_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            h->tune_ms[li][k] = ms / 3.0;
-            if (ms < best) { best = ms; best_rw = rws[k]; }
+            H2_CUDA(cudaEventRecord(ev[0], 0));
+            for (int it = 0; it < 5; ++it) {
+                launch_rows<A>(R, h->ops, h->vec, 0, 0);
+                H2_CUDA(cudaEventRecord(ev[it + 1], 0));
+            }
+            H2_CUDA(cudaEventSynchronize(ev[5]));
+            double best = 1e30;
+            for (int it = 0; it < 5; ++it) {
+                float ms = 0.f;
+                H2_CUDA(cudaEventElapsedTime(&ms, ev[it], ev[it + 1]));
+                best = std::min(best, double(ms));
+            }
+            t[k] = best;
+            h->tune_ms[li][k] = best;
         }
-        R.rw = best_rw;
+        int pick = 1;                       // 4 rows per warp
+        for (int k = 0; k < 3; ++k)
+            if (t[k] < 0.97 * t[pick]) pick = k;
+        R.rw = rws[pick];
     }
-    H2_CUDA(cudaEventDestroy(e0));
-    H2_CUDA(cudaEventDestroy(e1));
+    for (auto& e : ev) H2_CUDA(cudaEventDestroy(e));
     H2_CUDA(cudaGetLastError());
     return H2_OK;
 }
@@ -1427,5 +1439,477 @@ extern "C" void h2_batch_destroy(h2_batch b) {
     if (!b) return;
     cudaDeviceSynchronize();
     delete b;   // the destructor releases the graph, stream, events and memory
+}
+
+// ---------------------------------------------------------------------------
+// Served solves: a continuous-batching GMRES server over resident geometries.
+// Requests are admitted while their Krylov workspace fits the device budget;
+// every tick advances each active request by one GMRES step; the products of
+// all active requests on one geometry run as one multi-RHS product (their
+// vectors are its columns), and geometries run on their own streams.
+namespace {
+
+enum ReqState { RQ_RESIDUAL = 0, RQ_ARNOLDI = 1 };
+
+struct Req {
+    int64_t id = 0;
+    int g = 0;
+    double shift = 0, scale = 1, rtol = 1e-8;
+    int maxit = 1000;
+    std::vector<double> f;                 // host copy of the right-hand side
+    std::vector<double> xh;                // host solution when done
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    size_t ws_off = 0, ws_len = 0;         // workspace slice (doubles) of the pool
+    double *V = nullptr, *w = nullptr, *x = nullptr, *b = nullptr, *part = nullptr, *hd = nullptr;
+    double* hv = nullptr;                  // pinned host projections (m + 1)
+    int state = RQ_RESIDUAL, j = 0, iters = 0, restarts = 0;
+    double beta = 0, bnorm = 0, est = 1, relres = 1;
+    bool done = false, converged = false, xzero = true;
+    std::vector<double> H, cs, sn, gv, h1;
+};
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct h2_server_s {
+    std::vector<h2_handle> geoms;
+    std::vector<cudaStream_t> streams;
+    std::vector<double*> Xg, Yg;           // per geometry: N x max_active staging
+    int m = 50, max_active = 16;
+    double* pool = nullptr;
+    size_t pool_len = 0;                   // doubles
+    std::map<size_t, size_t> free_list;    // offset -> length (doubles)
+    double* pinned = nullptr;              // max_active x (m + 1) host projections
+    std::vector<int> pinned_free;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req*> queue;
+    std::vector<Req*> active;
+    std::map<int64_t, Req*> reqs;
+    int64_t next_id = 1;
+    bool stop = false;
+    std::thread worker;
+    std::string worker_error;
+    h2_server_stats stats = {};           // admission counters (under mu)
+    std::atomic<int64_t> ticks{0}, products{0}, product_columns{0};
+};
+
+namespace {
+
+bool ws_alloc(h2_server S, size_t n, size_t* off) {
+    for (auto it = S->free_list.begin(); it != S->free_list.end(); ++it) {
+        if (it->second >= n) {
+            *off = it->first;
+            const size_t rest = it->second - n;
+            const size_t o2 = it->first + n;
+            S->free_list.erase(it);
+            if (rest) S->free_list[o2] = rest;
+            return true;
+        }
+    }
+    return false;
+}
+
+void ws_free(h2_server S, size_t off, size_t n) {
+    auto it = S->free_list.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != S->free_list.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        S->free_list.erase(nx);
+    }
+    if (it != S->free_list.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            S->free_list.erase(it);
+        }
+    }
+}
+
+size_t req_doubles(h2_server S, int64_t N) {
+    const size_t m = size_t(S->m);
+    return size_t(N) * (m + 1) + 3 * size_t(N) + size_t(h2::kDotBlocks) * (m + 1) + (m + 1);
+}
+
+// y = A x for every request in rs (all on geometry g): one multi-RHS product.
+int serve_products(h2_server S, int g, const std::vector<std::pair<Req*, const double*>>& rs) {
+    h2_handle h = S->geoms[g];
+    cudaStream_t st = S->streams[g];
+    const int64_t N = h->host.tree.N;
+    const int k = int(rs.size());
+    for (int c = 0; c < k; ++c)
+        H2_CUDA(cudaMemcpyAsync(S->Xg[g] + int64_t(c) * N, rs[c].second, sizeof(double) * N,
+                                cudaMemcpyDeviceToDevice, st));
+    const int stor = h->host.storage;
+    int rc = (stor == H2_F64)   ? matvec_one<h2::F64>(h, S->Xg[g], N, S->Yg[g], N, k, st)
+             : (stor == H2_F32) ? matvec_one<h2::F32>(h, S->Xg[g], N, S->Yg[g], N, k, st)
+                                : matvec_one<h2::DF>(h, S->Xg[g], N, S->Yg[g], N, k, st);
+    if (rc != H2_OK) return rc;
+    for (int c = 0; c < k; ++c) {
+        Req* r = rs[c].first;
+        // w = shift x + scale K~ x
+        h2::k_axpbyz<<<nblocks(N, 256), 256, 0, st>>>(r->shift, rs[c].second, r->scale,
+                                                        S->Yg[g] + int64_t(c) * N, r->w, N);
+    }
+    S->products++;
+    S->product_columns += k;
+    return H2_OK;
+}
+
+void dots_async(h2_server S, Req* r, const double* Vm, int nvec, const double* w, cudaStream_t st) {
+    const int64_t N = S->geoms[r->g]->host.tree.N;
+    h2::k_multidot<<<h2::kDotBlocks, h2::kDotThreads, 0, st>>>(Vm, N, nvec, w, N, r->part);
+    h2::k_reduce_partials<<<nblocks(nvec, 128), 128, 0, st>>>(r->part, h2::kDotBlocks, nvec, r->hd);
+    cudaMemcpyAsync(r->hv, r->hd, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st);
+}
+
+int sync_all(h2_server S) {
+    for (cudaStream_t st : S->streams) H2_CUDA(cudaStreamSynchronize(st));
+    return H2_OK;
+}
+
+// One tick: every active request advances by one product and its GMRES step.
+int serve_tick(h2_server S, std::vector<Req*>& act) {
+    const int m = S->m;
+    // phase A: products (residual b - A x, or the next Arnoldi vector)
+    std::map<int, std::vector<std::pair<Req*, const double*>>> by_g;
+    for (Req* r : act) {
+        const int64_t N = S->geoms[r->g]->host.tree.N;
+        if (r->state == RQ_RESIDUAL) {
+            if (r->xzero) {
+                H2_CUDA(cudaMemsetAsync(r->w, 0, sizeof(double) * N, S->streams[r->g]));
+                continue;
+            }
+            by_g[r->g].push_back({r, r->x});
+        } else {
+            by_g[r->g].push_back({r, r->V + int64_t(r->j) * N});
+        }
+    }
+    for (auto& kv : by_g) H2_TRY(serve_products(S, kv.first, kv.second));
+    // phase B: first projections / residual norms
+    for (Req* r : act) {
+        const int64_t N = S->geoms[r->g]->host.tree.N;
+        cudaStream_t st = S->streams[r->g];
+        if (r->state == RQ_RESIDUAL) {
+            h2::k_axpbyz<<<nblocks(N, 256), 256, 0, st>>>(1.0, r->b, -1.0, r->w, r->V, N);  // V0 = b - A x
+            dots_async(S, r, r->V, 1, r->V, st);
+        } else {
+            dots_async(S, r, r->V, r->j + 1, r->w, st);
+        }
+    }
+    H2_TRY(sync_all(S));
+    std::vector<Req*> arn;
+    for (Req* r : act) {
+        const int64_t N = S->geoms[r->g]->host.tree.N;
+        cudaStream_t st = S->streams[r->g];
+        if (r->state == RQ_RESIDUAL) {
+            r->beta = std::sqrt(std::max(r->hv[0], 0.0));
+            r->relres = r->beta / r->bnorm;
+            if (r->beta <= r->rtol * r->bnorm || r->iters >= r->maxit) {
+                r->converged = r->beta <= r->rtol * r->bnorm;
+                r->done = true;
+                continue;
+            }
+            if (!r->xzero) r->restarts++;
+            h2::k_axpby<<<nblocks(N, 256), 256, 0, st>>>(0.0, r->V, 1.0 / r->beta, r->V, N);
+            std::fill(r->gv.begin(), r->gv.end(), 0.0);
+            r->gv[0] = r->beta;
+            r->j = 0;
+            r->state = RQ_ARNOLDI;
+            r->xzero = false;
+        } else {
+            std::copy(r->hv, r->hv + r->j + 1, r->h1.begin());
+            cudaMemcpyAsync(r->hd, r->h1.data(), sizeof(double) * (r->j + 1), cudaMemcpyHostToDevice, st);
+            h2::k_gemv_cols<<<nblocks(N, 256), 256, 0, st>>>(r->V, N, r->j + 1, r->hd, -1.0, r->w, N);
+            dots_async(S, r, r->V, r->j + 1, r->w, st);
+            arn.push_back(r);
+        }
+    }
+    if (arn.empty()) return H2_OK;
+    H2_TRY(sync_all(S));
+    for (Req* r : arn) {
+        const int64_t N = S->geoms[r->g]->host.tree.N;
+        cudaStream_t st = S->streams[r->g];
+        for (int i = 0; i <= r->j; ++i) r->H[size_t(i) * m + r->j] = r->h1[i] + r->hv[i];
+        cudaMemcpyAsync(r->hd, r->hv, sizeof(double) * (r->j + 1), cudaMemcpyHostToDevice, st);
+        h2::k_gemv_cols<<<nblocks(N, 256), 256, 0, st>>>(r->V, N, r->j + 1, r->hd, -1.0, r->w, N);
+        dots_async(S, r, r->w, 1, r->w, st);
+    }
+    H2_TRY(sync_all(S));
+    for (Req* r : arn) {
+        const int64_t N = S->geoms[r->g]->host.tree.N;
+        cudaStream_t st = S->streams[r->g];
+        const int j = r->j;
+        const double hn = std::sqrt(std::max(r->hv[0], 0.0));
+        r->H[size_t(j + 1) * m + j] = hn;
+        if (hn > 0.0)
+            h2::k_axpbyz<<<nblocks(N, 256), 256, 0, st>>>(1.0 / hn, r->w, 0.0, r->w, r->V + int64_t(j + 1) * N, N);
+        for (int i = 0; i < j; ++i) {
+            const double h0 = r->H[size_t(i) * m + j], h1 = r->H[size_t(i + 1) * m + j];
+            r->H[size_t(i) * m + j] = r->cs[i] * h0 + r->sn[i] * h1;
+            r->H[size_t(i + 1) * m + j] = -r->sn[i] * h0 + r->cs[i] * h1;
+        }
+        const double a0 = r->H[size_t(j) * m + j], c0 = r->H[size_t(j + 1) * m + j];
+        const double den = std::hypot(a0, c0);
+        r->cs[j] = den > 0 ? a0 / den : 1.0;
+        r->sn[j] = den > 0 ? c0 / den : 0.0;
+        r->H[size_t(j) * m + j] = den;
+        r->H[size_t(j + 1) * m + j] = 0.0;
+        r->gv[j + 1] = -r->sn[j] * r->gv[j];
+        r->gv[j] = r->cs[j] * r->gv[j];
+        r->iters++;
+        r->est = std::fabs(r->gv[j + 1]) / r->bnorm;
+        const bool stop_cycle = r->est <= r->rtol || j + 1 == m || r->iters >= r->maxit || hn == 0.0;
+        if (!stop_cycle) {
+            r->j = j + 1;
+            continue;
+        }
+        // x += V y, then recompute the true residual in the next tick
+        std::vector<double> y(j + 1);
+        for (int i = j; i >= 0; --i) {
+            double t = r->gv[i];
+            for (int k2 = i + 1; k2 <= j; ++k2) t -= r->H[size_t(i) * m + k2] * y[k2];
+            y[i] = r->H[size_t(i) * m + i] != 0.0 ? t / r->H[size_t(i) * m + i] : 0.0;
+        }
+        std::copy(y.begin(), y.end(), r->hv);
+        cudaMemcpyAsync(r->hd, r->hv, sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st);
+        h2::k_gemv_cols<<<nblocks(N, 256), 256, 0, st>>>(r->V, N, j + 1, r->hd, 1.0, r->x, N);
+        r->state = RQ_RESIDUAL;
+    }
+    H2_CUDA(cudaGetLastError());
+    return H2_OK;
+}
+
+void serve_loop(h2_server S) {
+    cudaSetDevice(S->geoms[0]->device);
+    for (;;) {
+        std::vector<Req*> act;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            // admission: FIFO while the workspace fits and a slot is free
+            while (!S->queue.empty() && int(S->active.size()) < S->max_active) {
+                Req* r = S->queue.front();
+                size_t off = 0;
+                if (!ws_alloc(S, r->ws_len, &off)) break;
+                S->queue.pop_front();
+                r->ws_off = off;
+                r->t_admit = now_s();
+                S->active.push_back(r);
+                const int64_t N = S->geoms[r->g]->host.tree.N;
+                double* base = S->pool + off;
+                r->V = base;
+                r->w = base + N * (S->m + 1);
+                r->x = r->w + N;
+                r->b = r->x + N;
+                r->part = r->b + N;
+                r->hd = r->part + size_t(h2::kDotBlocks) * (S->m + 1);
+                const int slot = S->pinned_free.back();
+                S->pinned_free.pop_back();
+                r->hv = S->pinned + size_t(slot) * (S->m + 1);
+                r->ws_off = off;
+                r->H.assign(size_t(S->m + 1) * S->m, 0.0);
+                r->cs.assign(S->m, 0.0);
+                r->sn.assign(S->m, 0.0);
+                r->gv.assign(S->m + 1, 0.0);
+                r->h1.assign(S->m + 1, 0.0);
+                r->bnorm = 0;
+                for (double v : r->f) r->bnorm += v * v;
+                r->bnorm = std::sqrt(r->bnorm);
+                cudaStream_t st = S->streams[r->g];
+                cudaMemcpyAsync(r->b, r->f.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st);
+                cudaMemsetAsync(r->x, 0, sizeof(double) * N, st);
+                S->stats.admitted++;
+            }
+            S->stats.max_active = std::max<int64_t>(S->stats.max_active, int64_t(S->active.size()));
+            if (S->active.empty()) {
+                if (S->stop) return;
+                S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+                continue;
+            }
+            act = S->active;
+        }
+        // requests with a zero right-hand side finish at once
+        for (Req* r : act)
+            if (r->bnorm == 0.0) { r->done = true; r->converged = true; r->relres = 0.0; }
+        std::vector<Req*> run;
+        for (Req* r : act) if (!r->done) run.push_back(r);
+        if (!run.empty()) {
+            int rc = serve_tick(S, run);
+            S->ticks++;
+            if (rc != H2_OK) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->worker_error = h2_last_error();
+                for (Req* r : act) { r->done = true; r->converged = false; }
+            }
+        }
+        // retire finished requests
+        std::vector<Req*> fin;
+        for (Req* r : act) if (r->done) fin.push_back(r);
+        for (Req* r : fin) {
+            const int64_t N = S->geoms[r->g]->host.tree.N;
+            r->xh.resize(N);
+            cudaMemcpyAsync(r->xh.data(), r->x, sizeof(double) * N, cudaMemcpyDeviceToHost, S->streams[r->g]);
+        }
+        if (!fin.empty()) sync_all(S);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (Req* r : fin) {
+                r->t_done = now_s();
+                ws_free(S, r->ws_off, r->ws_len);
+                S->pinned_free.push_back(int((r->hv - S->pinned) / (S->m + 1)));
+                S->active.erase(std::find(S->active.begin(), S->active.end(), r));
+                S->stats.completed++;
+            }
+        }
+        if (!fin.empty()) S->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" int h2_server_create(const h2_handle* geoms, int ngeom, const h2_server_opts* opts,
+                                h2_server* out) {
+    g_err.clear();
+    if (!geoms || ngeom < 1 || !out) return fail(H2_E_INVALID_ARG, "NULL argument or no geometry");
+    *out = nullptr;
+    h2_server_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    std::unique_ptr<h2_server_s> S(new h2_server_s());
+    S->m = o.restart > 0 ? o.restart : 50;
+    S->max_active = o.max_active > 0 ? o.max_active : 16;
+    if (S->m > 1000 || S->max_active > 1024) return fail(H2_E_INVALID_ARG, "restart or max_active too large");
+    int64_t maxN = 0;
+    for (int g = 0; g < ngeom; ++g) {
+        if (!geoms[g] || !geoms[g]->on_device) return fail(H2_E_INVALID_ARG, "geometry handle not on the device");
+        if (geoms[g]->device != geoms[0]->device) return fail(H2_E_INVALID_ARG, "geometries on different devices");
+        S->geoms.push_back(geoms[g]);
+        maxN = std::max(maxN, geoms[g]->host.tree.N);
+    }
+    const size_t budget = o.workspace_bytes > 0 ? size_t(o.workspace_bytes)
+                                                : req_doubles(S.get(), maxN) * S->max_active * sizeof(double);
+    S->pool_len = budget / sizeof(double);
+    if (S->pool_len < req_doubles(S.get(), 1)) return fail(H2_E_INVALID_ARG, "workspace budget too small");
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, S->pool_len * sizeof(double));
+    if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    S->pool = static_cast<double*>(p);
+    S->free_list[0] = S->pool_len;
+    e = cudaMallocHost(&p, sizeof(double) * size_t(S->max_active) * (S->m + 1));
+    if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    S->pinned = static_cast<double*>(p);
+    for (int k = S->max_active - 1; k >= 0; --k) S->pinned_free.push_back(k);
+    for (int g = 0; g < ngeom; ++g) {
+        cudaStream_t st;
+        H2_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        S->streams.push_back(st);
+        const int64_t N = geoms[g]->host.tree.N;
+        double *x = nullptr, *y = nullptr;
+        H2_CUDA(cudaMalloc(&x, sizeof(double) * N * S->max_active));
+        H2_CUDA(cudaMalloc(&y, sizeof(double) * N * S->max_active));
+        S->Xg.push_back(x);
+        S->Yg.push_back(y);
+        int rc = grow_vec(geoms[g], S->max_active);
+        if (rc != H2_OK) return rc;
+        geoms[g]->profile = false;
+    }
+    S->stats.workspace_bytes = int64_t(S->pool_len * sizeof(double));
+    h2_server_s* raw = S.get();
+    S->worker = std::thread([raw] { serve_loop(raw); });
+    *out = S.release();
+    return H2_OK;
+}
+
+extern "C" int h2_server_submit(h2_server S, int geom, double shift, double scale, const double* f,
+                                double rtol, int maxit, int64_t* ticket) {
+    g_err.clear();
+    if (!S || !f || !ticket) return fail(H2_E_INVALID_ARG, "NULL argument");
+    if (geom < 0 || geom >= int(S->geoms.size())) return fail(H2_E_INVALID_ARG, "unknown geometry");
+    if (!(rtol > 0.0 && rtol < 1.0) || maxit < 1) return fail(H2_E_INVALID_ARG, "rtol or maxit out of range");
+    const int64_t N = S->geoms[geom]->host.tree.N;
+    std::unique_ptr<Req> r(new Req());
+    r->g = geom;
+    r->shift = shift;
+    r->scale = scale;
+    r->rtol = rtol;
+    r->maxit = maxit;
+    r->f.assign(f, f + N);
+    r->ws_len = req_doubles(S, N);
+    if (r->ws_len > S->pool_len) return fail(H2_E_OOM, "request workspace exceeds the server's budget");
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (!S->worker_error.empty()) return fail(H2_E_CUDA, "server stopped: " + S->worker_error);
+        Req* raw = r.release();
+        raw->id = S->next_id++;
+        *ticket = raw->id;
+        S->queue.push_back(raw);
+        S->reqs[raw->id] = raw;
+        S->stats.submitted++;
+    }
+    S->cv_work.notify_one();
+    return H2_OK;
+}
+
+extern "C" int h2_server_wait(h2_server S, int64_t ticket, double* x, h2_request_stats* st) {
+    g_err.clear();
+    if (!S) return fail(H2_E_INVALID_ARG, "NULL server");
+    Req* r = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return fail(H2_E_INVALID_ARG, "unknown ticket");
+        r = it->second;
+        S->cv_done.wait(lk, [&] { return r->t_done > 0.0; });
+        S->reqs.erase(it);
+    }
+    std::unique_ptr<Req> own(r);
+    if (x) std::copy(r->xh.begin(), r->xh.end(), x);
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->converged = r->converged ? 1 : 0;
+        st->iterations = r->iters;
+        st->restarts = r->restarts;
+        st->rel_residual = r->relres;
+        st->queue_seconds = r->t_admit - r->t_submit;
+        st->latency_seconds = r->t_done - r->t_submit;
+    }
+    if (!r->converged) return fail(H2_E_NOT_CONVERGED, "request stopped before reaching rtol");
+    return H2_OK;
+}
+
+extern "C" int h2_server_stats_get(h2_server S, h2_server_stats* st) {
+    g_err.clear();
+    if (!S || !st) return fail(H2_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    *st = S->stats;
+    st->ticks = S->ticks.load();
+    st->products = S->products.load();
+    st->product_columns = S->product_columns.load();
+    st->queued = int64_t(S->queue.size());
+    st->active = int64_t(S->active.size());
+    return H2_OK;
+}
+
+extern "C" void h2_server_destroy(h2_server S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->queue.clear();
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    cudaDeviceSynchronize();
+    for (auto& kv : S->reqs) delete kv.second;
+    for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
+    for (double* p : S->Xg) cudaFree(p);
+    for (double* p : S->Yg) cudaFree(p);
+    if (S->pool) cudaFree(S->pool);
+    if (S->pinned) cudaFreeHost(S->pinned);
+    delete S;
 }
 

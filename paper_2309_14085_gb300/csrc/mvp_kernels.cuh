@@ -196,14 +196,17 @@ __global__ void k_scatter(const typename A::V* __restrict__ phi, int nrhs,
 // feeds NR multiply-adds and one staged coefficient RW of them, and each lane
 // keeps 2 RW independent loads in flight.  Segments are sorted by column
 // (seg_col = first column of each).
-template <class A, int RW, int NR>
+template <class A, int RW, int NR, bool ONE>
 __global__ void __launch_bounds__(256) k_rowgemv(
     int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
     const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
     const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
     const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
     const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate,
-    int nrhs, int c0) {
+    int nrhs_arg, int c0_arg) {
+    // ONE: a single right-hand side (nrhs = 1, c0 = 0 known at compile time)
+    const int nrhs = ONE ? 1 : nrhs_arg;
+    const int c0 = ONE ? 0 : c0_arg;
     using V = typename A::V;
     using L = typename A::L;
     constexpr int W = A::W;
