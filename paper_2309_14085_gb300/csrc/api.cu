@@ -200,9 +200,15 @@ int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize
 template <class A, int RW, int NR>
 void launch_rows_rw(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate,
                     int nrhs, int c0) {
-    h2::k_rowgemv<A, RW, NR, false><<<unsigned(R.n), 256, 0, s>>>(
-            R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
-            static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate, nrhs, c0);
+    if (NR == 1 && nrhs == 1)
+        h2::k_rowgemv1<A, RW><<<unsigned(R.n), 256, 0, s>>>(
+                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
+                static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate);
+    else
+        h2::k_rowgemv<A, RW, NR><<<unsigned(R.n), 256, 0, s>>>(
+                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
+                static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate,
+                nrhs, c0);
 }
 
 // Largest RHS tile: 4 columns in fp32, 2 in fp64 / double-float.  Wider tiles

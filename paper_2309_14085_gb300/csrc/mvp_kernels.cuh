@@ -196,17 +196,14 @@ __global__ void k_scatter(const typename A::V* __restrict__ phi, int nrhs,
 // feeds NR multiply-adds and one staged coefficient RW of them, and each lane
 // keeps 2 RW independent loads in flight.  Segments are sorted by column
 // (seg_col = first column of each).
-template <class A, int RW, int NR, bool ONE>
+template <class A, int RW, int NR>
 __global__ void __launch_bounds__(256) k_rowgemv(
     int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
     const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
     const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
     const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
     const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate,
-    int nrhs_arg, int c0_arg) {
-    // ONE: a single right-hand side (nrhs = 1, c0 = 0 known at compile time)
-    const int nrhs = ONE ? 1 : nrhs_arg;
-    const int c0 = ONE ? 0 : c0_arg;
+    int nrhs, int c0) {
     using V = typename A::V;
     using L = typename A::L;
     constexpr int W = A::W;
@@ -263,26 +260,35 @@ __global__ void __launch_bounds__(256) k_rowgemv(
                     if (ok[w]) a0[w] = __ldg(arow[w] + k0 + k);
                     if (ok[w] && two) a1[w] = __ldg(arow[w] + k0 + k + kWarp);
                 }
+                // first k-step for every z, then the second: the summation
+                // order of k_rowgemv1, so each column matches it bit for bit
 #pragma unroll
                 for (int z = 0; z < W; ++z) {
-                    V x0[NR], x1[NR];
+                    V x0[NR];
 #pragma unroll
-                    for (int c = 0; c < NR; ++c) {
-                        x0[c] = xs[(k * W + z) * NR + c];
-                        x1[c] = two ? xs[((k + kWarp) * W + z) * NR + c] : A::zero();
-                    }
+                    for (int c = 0; c < NR; ++c) x0[c] = xs[(k * W + z) * NR + c];
 #pragma unroll
                     for (int w = 0; w < RW; ++w)
                         if (ok[w]) {
                             const auto s0 = A::lget(a0[w], z);
 #pragma unroll
                             for (int c = 0; c < NR; ++c) acc[w][c] = A::mac(acc[w][c], s0, x0[c]);
-                            if (two) {
+                        }
+                }
+                if (two) {
+#pragma unroll
+                    for (int z = 0; z < W; ++z) {
+                        V x1[NR];
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) x1[c] = xs[((k + kWarp) * W + z) * NR + c];
+#pragma unroll
+                        for (int w = 0; w < RW; ++w)
+                            if (ok[w]) {
                                 const auto s1 = A::lget(a1[w], z);
 #pragma unroll
                                 for (int c = 0; c < NR; ++c) acc[w][c] = A::mac(acc[w][c], s1, x1[c]);
                             }
-                        }
+                    }
                 }
             }
         }
@@ -298,6 +304,95 @@ __global__ void __launch_bounds__(256) k_rowgemv(
                     *yo = accumulate ? A::add(*yo, sum) : sum;
                 }
             }
+        }
+    }
+}
+
+// The same block-row GEMV for a single right-hand side (nrhs = 1): the staged
+// chunk is contiguous, so each lane reads its W coefficients of both k-steps
+// with two 16-byte shared loads before the row loop, and each row's W
+// multiply-adds of a k-step run back to back on one accumulator.
+template <class A, int RW>
+__global__ void __launch_bounds__(256) k_rowgemv1(
+    int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
+    const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
+    const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
+    const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
+    const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate) {
+    using V = typename A::V;
+    using L = typename A::L;
+    constexpr int W = A::W;
+    constexpr int C = 4096 * 8 / int(sizeof(V));   // 32 KB of staged coefficients
+    constexpr int NW = 8;
+    static_assert(C % (2 * kWarp * W) == 0, "chunk must hold whole warp steps");
+    __shared__ __align__(16) V xs[C];
+    const int64_t t = blockIdx.x;
+    if (t >= ntask) return;
+    const int kp = kpad[t];
+    const int nr = rows[t];
+    const int64_t e0 = seg_ptr[t], e1 = seg_ptr[t + 1];
+    const int ktot = (e1 > e0) ? seg_col[e1 - 1] + seg_len[e1 - 1] : 0;
+    const typename A::S* Am = ops + aoff[t];
+    V* y = vec + dst[t];
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    for (int r0 = 0; r0 < nr; r0 += NW * RW) {
+        V acc[RW];
+        bool ok[RW];
+        const L* arow[RW];
+#pragma unroll
+        for (int w = 0; w < RW; ++w) {
+            acc[w] = A::zero();
+            const int row = r0 + warp + NW * w;
+            ok[w] = row < nr;
+            arow[w] = reinterpret_cast<const L*>(Am + int64_t(ok[w] ? row : 0) * kp);
+        }
+        int64_t ef = e0;
+        for (int ch = 0; ch < kp; ch += C) {
+            const int cw = min(C, kp - ch);
+            __syncthreads();
+            while (ef < e1 && seg_col[ef] + seg_len[ef] <= ch) ++ef;
+            for (int64_t e = ef; e < e1; ++e) {
+                const int sc = seg_col[e];
+                if (sc >= ch + cw) break;
+                const int lo = max(sc, ch), hi = min(sc + seg_len[e], ch + cw);
+                const V* src = vec + seg_off[e] + (lo - sc);
+                for (int j = threadIdx.x; j < hi - lo; j += blockDim.x) xs[lo - ch + j] = src[j];
+            }
+            for (int j = max(ktot - ch, 0) + threadIdx.x; j < cw; j += blockDim.x) xs[j] = A::zero();
+            __syncthreads();
+            const int nv = cw / W, k0 = ch / W;
+            for (int k = lane; k < nv; k += 2 * kWarp) {
+                const bool two = k + kWarp < nv;
+                L a0[RW], a1[RW];
+#pragma unroll
+                for (int w = 0; w < RW; ++w) {
+                    if (ok[w]) a0[w] = __ldg(arow[w] + k0 + k);
+                    if (ok[w] && two) a1[w] = __ldg(arow[w] + k0 + k + kWarp);
+                }
+                V x0[W], x1[W];
+#pragma unroll
+                for (int z = 0; z < W; ++z) {
+                    x0[z] = xs[k * W + z];
+                    x1[z] = two ? xs[(k + kWarp) * W + z] : A::zero();
+                }
+#pragma unroll
+                for (int w = 0; w < RW; ++w)
+                    if (ok[w]) {
+#pragma unroll
+                        for (int z = 0; z < W; ++z) acc[w] = A::mac(acc[w], A::lget(a0[w], z), x0[z]);
+                        if (two) {
+#pragma unroll
+                            for (int z = 0; z < W; ++z) acc[w] = A::mac(acc[w], A::lget(a1[w], z), x1[z]);
+                        }
+                    }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < RW; ++w) {
+            if (!ok[w]) continue;
+            const V sum = warp_sum<A>(acc[w]);
+            const int row = r0 + warp + NW * w;
+            if (lane == 0) y[row] = accumulate ? A::add(y[row], sum) : sum;
         }
     }
 }
