@@ -377,6 +377,134 @@ def bench_batched(args):
     print(json.dumps(out))
 
 
+def bench_served(args):
+    """Served RBF interpolation solves (sigma I + K) c = f, K the inverse
+    multiquadric 1/sqrt(1 + (r/0.1)^2), sigma = 1e-2, on resident geometries
+    (inputs.served_geometries), requests arriving as a Poisson stream.  Four
+    forms on the same stream, each to the same fp64 relative residual:
+      plain_fp64    one fp64 GMRES solve at a time (h2_gmres), first come first served;
+      served_fp64   the continuous-batching server on the fp64 operators;
+      served_df64   the server on double-float copies of the operators
+                    (h2_convert; float pairs on the FP32 pipe) with fp64 residuals;
+      served_f32    the server on fp32 copies with fp64 residuals; requests whose
+                    shift is too small for fp32 (the server's measured rule)
+                    iterate on the fp64 operator.
+    value = solves/s of served_df64 over the stream (first arrival to last
+    completion); latency = submit to solution on the host."""
+    import queue
+    import threading
+
+    import torch
+
+    from paper_2309_14085_gb300 import H2Matrix, H2Server, inputs
+    geo = inputs.served_geometries(args.geometries)
+    t0 = time.perf_counter()
+    f64s = [H2Matrix(gm["points"], "imq", leaf_size=64, tol=1e-8, kparam=0.1) for gm in geo]
+    f32s = [m.convert("f32") for m in f64s]
+    dfs = [m.convert("df64") for m in f64s]
+    build_s = time.perf_counter() - t0
+    dev_bytes = sum(m.info()["bytes_device"] for m in f64s + f32s + dfs)
+    arr, gid = inputs.poisson_arrivals(args.requests, args.rate, len(geo))
+    sigma, rtol, restart, maxit = 1e-2, 1e-8, args.restart, 20000
+    fs = [gm["f"] for gm in geo]
+
+    def summary(lat, its, res, span, extra=None):
+        lat = np.asarray(lat)
+        o = {"solves_per_s": round(len(lat) / span, 3),
+             "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 2),
+             "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 2),
+             "iterations_median": float(np.median(its)), "max_rel_residual": float(max(res)),
+             "span_s": round(span, 3)}
+        if extra:
+            o.update(extra)
+        return o
+
+    def run_plain():
+        for g, m in enumerate(f64s):          # warm-up: Krylov workspace of each geometry
+            m.gmres(torch.tensor(fs[g], device="cuda"), shift=sigma, rtol=rtol, restart=restart,
+                    maxit=maxit)
+        torch.cuda.synchronize()
+        lat, its, res = [], [], []
+        start = time.perf_counter()
+        for i in range(len(arr)):
+            dt = start + arr[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            g = int(gid[i])
+            b = torch.tensor(fs[g], device="cuda")
+            x, st = f64s[g].gmres(b, shift=sigma, rtol=rtol, restart=restart, maxit=maxit)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - (start + arr[i]))
+            its.append(st["iterations"])
+            res.append(st["rel_residual"])
+        return summary(lat, its, res, time.perf_counter() - start)
+
+    def run_server(mats, residual):
+        S = H2Server(mats, restart=restart, max_active=args.max_active, residual=residual)
+        for g in range(len(mats)):            # warm-up: one request per geometry
+            S.wait(S.submit(g, fs[g], shift=sigma, rtol=rtol, maxit=maxit))
+        st0 = S.stats()
+        q = queue.Queue()
+        start = time.perf_counter()
+
+        def submitter():
+            for i in range(len(arr)):
+                dt = start + arr[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                g = int(gid[i])
+                q.put((g, S.submit(g, fs[g], shift=sigma, rtol=rtol, maxit=maxit)))
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, its, res, qs, ops = [], [], [], [], []
+        for _ in range(len(arr)):
+            g, t = q.get()
+            x, st = S.wait(t)
+            ops.append(st["op"])
+            lat.append(st["latency_seconds"])
+            qs.append(st["queue_seconds"])
+            its.append(st["iterations"])
+            res.append(st["rel_residual"])
+        span = time.perf_counter() - start
+        th.join()
+        st1 = S.stats()
+        S.close()
+        extra = {"queue_p50_ms": round(1e3 * float(np.percentile(qs, 50)), 2),
+                 "max_active_seen": st1["max_active"],
+                 "products": st1["products"] - st0["products"],
+                 "product_columns": st1["product_columns"] - st0["product_columns"],
+                 "ticks": st1["ticks"] - st0["ticks"],
+                 "requests_by_operator": {"inner": ops.count(0), "fp64_by_rule": ops.count(1),
+                                          "fp64_after_fallback": ops.count(2)}}
+        return summary(lat, its, res, span, extra)
+
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    plain = run_plain()
+    served64 = run_server(f64s, None)
+    mixed = run_server(dfs, f64s)
+    served32 = run_server(f32s, f64s)
+    clk = clocks.stop()
+    out = {"metric": "served RBF solves/s (p50/p99 latency)", "value": mixed["solves_per_s"],
+           "unit": "solves/s", "n_gpus": 1, "steps": len(arr), "warmup": len(geo),
+           "ms_per_step": round(1e3 / mixed["solves_per_s"], 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "df64 operators (float pairs); f64 GMRES vectors and residuals",
+           "data": "synthetic (seeded uniform points, f = sin(3 x1) cos(2 x2), Poisson arrivals)",
+           "config": {"workload": "c5_served", "kernel": "inverse multiquadric, c = 0.1",
+                      "sigma": sigma, "eps": 1e-8, "leaf_size": 64, "rtol": rtol,
+                      "restart": restart, "max_active": args.max_active,
+                      "arrival_rate_per_s": args.rate, "requests": len(arr),
+                      "geometries": [{"d": gm["d"], "N": gm["N"]} for gm in geo],
+                      "build_seconds": round(build_s, 1), "device_bytes": dev_bytes,
+                      "l2": "operators larger than L2 (no flush)"},
+           "clocks": clk, "served_df64": mixed, "served_f32": served32, "served_fp64": served64,
+           "plain_fp64": plain}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,6 +521,11 @@ def main():
                     help="other storage modes measured in the same run (comma list, '' for none)")
     ap.add_argument("--oracle-child", nargs=2, default=None)
     ap.add_argument("--instances", type=int, default=64, help="batched workload: instance count")
+    ap.add_argument("--geometries", type=int, default=6, help="served workload: geometries")
+    ap.add_argument("--requests", type=int, default=48, help="served workload: requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="served workload: arrivals per s")
+    ap.add_argument("--max-active", type=int, default=16, help="served workload: active requests")
+    ap.add_argument("--restart", type=int, default=1000, help="served workload: GMRES restart")
     args = ap.parse_args()
     if args.oracle_child:
         oracle_rows_child(args.oracle_child[0], float(args.oracle_child[1]))
@@ -400,6 +533,10 @@ def main():
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+
+    if args.workload == "c5_served":
+        bench_served(args)
+        return
 
     if args.workload == "c4_batched":
         if args.storage == "f64" and "--storage" not in sys.argv:

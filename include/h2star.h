@@ -107,6 +107,22 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size,
              double tol, int variant, const h2_build_opts* opts, h2_handle* out);
 
 /*
+ * h2_convert -- a second device copy of the same compressed operator in another
+ * storage precision, without repeating the construction: the tree, lists,
+ * pivots and packed operators of `src` are copied on the host and uploaded in
+ * `storage` (H2_F64, H2_F32 or H2_DF64) to the current CUDA device.  The result
+ * is an independent handle (h2_destroy it separately); its products equal those
+ * of a handle built by h2_build with the same arguments, this storage and
+ * near_mode 2 (src stores its near-field blocks) or 1 (src evaluates them on
+ * the fly).  Mixed-precision solves pair the two: h2_gmres(converted fp32,
+ * fp64 src, ...), or a server with residual handles.
+ * Errors: H2_E_INVALID_ARG, H2_E_UNSUPPORTED (H2_DF64 from a source without
+ * stored near-field blocks, or from (H2+H)*), H2_E_OOM, H2_E_CUDA,
+ * H2_E_NO_DEVICE.
+ */
+int h2_convert(h2_handle src, int storage, h2_handle* out);
+
+/*
  * h2_matvec -- Y = K~ X for nrhs right-hand sides (§5.1.2 / §5.2.2 / App. A.2).
  *
  *   X      device, fp64, column-major N x nrhs with leading dimension ldx >= N,
@@ -200,6 +216,9 @@ typedef struct {
     double  rel_residual;      /* ||b - A x||_2 / ||b||_2, recomputed in fp64 at exit  */
     double  rel_residual_est;  /* the last GMRES least-squares estimate                */
     double  seconds;           /* wall time of the call (it synchronises the stream)   */
+    int     fallback;          /* 1 if refinement stopped contracting and the solve was
+                                  finished by fp64 GMRES on h_res                        */
+    int     pad_;
 } h2_gmres_stats;
 
 /*
@@ -218,7 +237,10 @@ typedef struct {
  *          fp64 storage when h is fp32): then the solve is an iterative
  *          refinement -- residuals r = b - A x are recomputed in fp64 with
  *          h_res, each correction comes from GMRES on h -- so it reaches an
- *          fp64 tolerance while the iterations use the faster product.
+ *          fp64 tolerance while the iterations use the faster product.  A
+ *          correction that does not halve the fp64 residual (h too coarse for
+ *          this system: its error exceeds the smallest singular value) is
+ *          undone, and GMRES on h_res finishes the solve (st->fallback = 1).
  *   b, x   device, fp64, N entries in user order (x overwritten).
  *   rtol   relative residual target in (0, 1); restart in [1, 1000]; maxit >= 1
  *          bounds the GMRES iterations over all cycles and refinements.
@@ -305,6 +327,9 @@ typedef struct {
                                   footprint); 0 = max_active requests of the largest N  */
     int     restart;           /* GMRES(restart) per request (default 50)               */
     int     max_active;        /* requests iterated together at most (default 16)       */
+    int     inner_policy;      /* with res_geoms: 0 = the measured admission rule below,
+                                  1 = every request starts on geoms[g] (guard only)     */
+    int     pad_;
 } h2_server_opts;
 
 typedef struct {
@@ -317,6 +342,10 @@ typedef struct {
 
 typedef struct {
     int    converged, iterations, restarts;
+    int    op;                 /* Arnoldi operator: 0 geoms[g] throughout; 1 res_geoms[g]
+                                  (geoms[g] error > |shift| / 10 for this request);
+                                  2 res_geoms[g] after a geoms[g] cycle that did not halve
+                                  the fp64 residual (that cycle is undone)              */
     double rel_residual;       /* ||f - A x|| / ||f||, recomputed at the end            */
     double queue_seconds;      /* submit -> admission                                   */
     double latency_seconds;    /* submit -> solution ready                              */
@@ -324,18 +353,40 @@ typedef struct {
 
 /*
  * h2_server_create -- start a solve server over resident geometries (handles
- * built by h2_build on the current device; they stay owned by the caller and
- * must outlive the server; each is used by the server only).  One worker
+ * built by h2_build or h2_convert on the current device; they stay owned by
+ * the caller and must outlive the server).  The server takes the handles for
+ * its lifetime: h2_matvec, h2_matvec_noalloc, h2_gmres and another server
+ * refuse them (H2_E_INVALID_ARG) until h2_server_destroy, and one handle may
+ * not serve two geometry slots (each has one coefficient buffer).  One worker
  * thread iterates all admitted requests together: each tick performs one
  * GMRES step (fp64 vectors, classical Gram-Schmidt twice) for every active
  * request, the products of the requests on one geometry running as a single
  * multi-RHS h2 product and different geometries on their own CUDA streams, so
  * their work overlaps on the device.  Requests that arrive while others run
- * join at the next tick once their Krylov workspace ((restart + 1 + 3) N
+ * join at the next tick once their Krylov workspace ((restart + 1 + 4) N
  * doubles) fits the budget and a slot is free (first come, first served).
+ *
+ *   geoms      host array of ngeom handles: the operators of the Arnoldi
+ *              products.
+ *   res_geoms  NULL, or host array of ngeom handles of the same geometries
+ *              (same N and point order, e.g. the fp64 source of an fp32
+ *              h2_convert copy; an entry may equal geoms[g]).  The residual
+ *              f - A x that starts every GMRES cycle and the final residual
+ *              then use res_geoms[g], so a request on an fp32 geometry reaches
+ *              an fp64 tolerance by iterative refinement: each cycle solves
+ *              for the correction until its own residual has dropped by 1e-5
+ *              (fp32; 1e-10 for other storage) or to rtol ||f||.  Two guards
+ *              keep every request convergent: at creation the server measures
+ *              delta_g = ||(K_geoms - K_res) v|| / ||v|| on one seeded random
+ *              vector, and (inner_policy 0) a request with shift != 0 and
+ *              delta_g |scale| > |shift| / 10 iterates on res_geoms[g] from the
+ *              start; a cycle on geoms[g] that does not halve the fp64 residual
+ *              is undone and the request continues on res_geoms[g]
+ *              (h2_request_stats.op tells which happened).
  * Errors: H2_E_INVALID_ARG, H2_E_OOM, H2_E_CUDA.
  */
-int h2_server_create(const h2_handle* geoms, int ngeom, const h2_server_opts* opts, h2_server* out);
+int h2_server_create(const h2_handle* geoms, const h2_handle* res_geoms, int ngeom,
+                     const h2_server_opts* opts, h2_server* out);
 
 /*
  * h2_server_submit -- queue a solve of (shift I + scale K~_geom) x = f to relative

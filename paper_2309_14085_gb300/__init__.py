@@ -24,7 +24,7 @@ VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2}
 STORAGE = {"f64": 0, "f32": 1, "df64": 2}
 NEAR = {None: 0, "fly": 1, "stored": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
-EXPORTED = ("h2_build", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
+EXPORTED = ("h2_build", "h2_convert", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
             "h2_batch_matvec", "h2_batch_info", "h2_batch_destroy", "h2_server_create",
             "h2_server_submit", "h2_server_wait", "h2_server_stats_get", "h2_server_destroy")
@@ -62,7 +62,7 @@ class GmresStats(ctypes.Structure):
                 ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("matvecs", ctypes.c_int64), ("matvecs_residual", ctypes.c_int64),
                 ("rel_residual", ctypes.c_double), ("rel_residual_est", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("fallback", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class BatchStats(ctypes.Structure):
@@ -75,7 +75,7 @@ class BatchStats(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("workspace_bytes", ctypes.c_int64), ("restart", ctypes.c_int),
-                ("max_active", ctypes.c_int)]
+                ("max_active", ctypes.c_int), ("inner_policy", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -86,7 +86,7 @@ class ServerStats(ctypes.Structure):
 
 class RequestStats(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int),
-                ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("restarts", ctypes.c_int), ("op", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("queue_seconds", ctypes.c_double), ("latency_seconds", ctypes.c_double)]
 
 
@@ -124,7 +124,9 @@ def lib():
         L.h2_batch_info.argtypes = [c_vp, ctypes.POINTER(BatchStats)]
         L.h2_batch_destroy.argtypes = [c_vp]
         L.h2_batch_destroy.restype = None
-        L.h2_server_create.argtypes = [c_vp, c_int, ctypes.POINTER(ServerOpts), ctypes.POINTER(c_vp)]
+        L.h2_convert.argtypes = [c_vp, c_int, ctypes.POINTER(c_vp)]
+        L.h2_server_create.argtypes = [c_vp, c_vp, c_int, ctypes.POINTER(ServerOpts),
+                                       ctypes.POINTER(c_vp)]
         L.h2_server_submit.argtypes = [c_vp, c_int, c_dbl, c_dbl, c_vp, c_dbl, c_int,
                                        ctypes.POINTER(c_i64)]
         L.h2_server_wait.argtypes = [c_vp, c_i64, c_vp, ctypes.POINTER(RequestStats)]
@@ -182,6 +184,16 @@ class H2Matrix:
         _check(lib().h2_build(P.ctypes.data, self.N, self.d, KERNELS[kernel], leaf_size, tol,
                               VARIANTS[variant], ctypes.byref(o), ctypes.byref(h)))
         self._h = h
+
+    def convert(self, storage):
+        """A second device copy of this operator in another storage ("f64",
+        "f32" or "df64"), without repeating the construction."""
+        h = ctypes.c_void_p()
+        _check(lib().h2_convert(self._h, STORAGE[storage], ctypes.byref(h)))
+        m = H2Matrix.__new__(H2Matrix)
+        m.N, m.d, m.kernel, m.variant, m.storage = self.N, self.d, self.kernel, self.variant, storage
+        m._h = h
+        return m
 
     # -- the product ---------------------------------------------------------
     def matvec(self, X, out=None, stream=None):
@@ -334,13 +346,25 @@ class H2Server:
     for its solution; requests that arrive while others run join the active
     set as workspace frees up."""
 
-    def __init__(self, geometries, workspace_bytes=0, restart=50, max_active=16):
+    def __init__(self, geometries, workspace_bytes=0, restart=50, max_active=16, residual=None,
+                 inner_policy=0):
+        """`residual`: None, or one H2Matrix per geometry (same points) whose
+        operator computes the residual that starts every GMRES cycle, e.g. the
+        fp64 source of fp32 geometries made by H2Matrix.convert("f32").
+        `inner_policy`: 0 admits a request on the inner operator only if its
+        measured error is below |shift| / 10; 1 always starts there."""
         self.geometries = list(geometries)
+        self.residual = list(residual) if residual is not None else None
         n = len(self.geometries)
         hs = (ctypes.c_void_p * n)(*[g._h.value for g in self.geometries])
-        o = ServerOpts(workspace_bytes, restart, max_active)
+        rs = None
+        if self.residual is not None:
+            if len(self.residual) != n:
+                raise ValueError("one residual matrix per geometry")
+            rs = (ctypes.c_void_p * n)(*[g._h.value for g in self.residual])
+        o = ServerOpts(workspace_bytes, restart, max_active, inner_policy, 0)
         h = ctypes.c_void_p()
-        _check(lib().h2_server_create(hs, n, ctypes.byref(o), ctypes.byref(h)))
+        _check(lib().h2_server_create(hs, rs, n, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
 
     def submit(self, geom, f, shift=0.0, scale=1.0, rtol=1e-8, maxit=1000):

@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <random>
 #include <thread>
 #include <string>
 #include <type_traits>
@@ -58,6 +59,7 @@ struct DevRowTasks {
 struct h2_handle_s {
     h2::Host host;
     bool on_device = false;
+    const struct h2_server_s* server = nullptr;   // the solve server using this handle
     int device = -1;
     size_t vsize = 8;             // sizeof coefficient type
     int64_t bytes_device = 0;
@@ -631,11 +633,52 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     return H2_OK;
 }
 
+int h2_convert(h2_handle src, int storage, h2_handle* out) {
+    g_err.clear();
+    if (!out) return fail(H2_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!src) return fail(H2_E_INVALID_ARG, "src is NULL");
+    if (storage != H2_F64 && storage != H2_F32 && storage != H2_DF64)
+        return fail(H2_E_INVALID_ARG, "unknown storage");
+    const bool stored = src->host.packed.near_stored;
+    if (storage == H2_DF64 && !stored)
+        return fail(H2_E_UNSUPPORTED, "df64 storage needs stored near-field blocks; the source "
+                                      "evaluates them on the fly");
+    if (storage == H2_DF64 && src->host.variant == H2_PLUS_H_STAR)
+        return fail(H2_E_UNSUPPORTED, "(H2+H)* is built for fp64 and fp32 storage");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(H2_E_NO_DEVICE, "no CUDA device");
+    }
+    std::unique_ptr<h2_handle_s> h;
+    try {
+        h.reset(new h2_handle_s());
+        h->host = src->host;
+    } catch (const std::bad_alloc&) {
+        return fail(H2_E_OOM, "host allocation failed");
+    }
+    h->host.storage = storage;
+    h->host.near_mode = stored ? 2 : 1;
+    H2_CUDA(cudaGetDevice(&h->device));
+    int rc = (storage == H2_F64)   ? upload<h2::F64>(h.get())
+             : (storage == H2_F32) ? upload<h2::F32>(h.get())
+                                   : upload<h2::DF>(h.get());
+    if (rc != H2_OK) {
+        h2_destroy(h.release());
+        return rc;
+    }
+    h->on_device = true;
+    *out = h.release();
+    return H2_OK;
+}
+
 int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int nrhs,
               void* stream) {
     g_err.clear();
     if (!h) return fail(H2_E_INVALID_ARG, "handle is NULL");
     if (!h->on_device) return fail(H2_E_NO_DEVICE, "handle was built host-only");
+    if (h->server) return fail(H2_E_INVALID_ARG, "handle is in use by a solve server");
     const int64_t N = h->host.tree.N;
     if (!X || !Y) return fail(H2_E_INVALID_ARG, "X or Y is NULL");
     if (nrhs < 1 || nrhs > 64) return fail(H2_E_INVALID_ARG, "nrhs must be in [1, 64]");
@@ -816,6 +859,7 @@ extern "C" int h2_matvec_noalloc(h2_handle h, const double* X, double* Y, void* 
     g_err.clear();
     if (!h) return fail(H2_E_INVALID_ARG, "handle is NULL");
     if (!h->on_device) return fail(H2_E_NO_DEVICE, "handle was built host-only");
+    if (h->server) return fail(H2_E_INVALID_ARG, "handle is in use by a solve server");
     if (!X || !Y) return fail(H2_E_INVALID_ARG, "X or Y is NULL");
     const h2::Packed& P = h->host.packed;
     const size_t vec_bytes = (size_t(P.veclen) * h->vsize + 255) / 256 * 256;
@@ -897,7 +941,7 @@ int gm_workspace(h2_handle h, int m) {
 int gm_dots(h2_handle h, const double* V, int64_t ldv, int nvec, const double* w, double* out,
             cudaStream_t s) {
     const int64_t N = h->host.tree.N;
-    h2::k_multidot<<<h2::kDotBlocks, h2::kDotThreads, 0, s>>>(V, ldv, nvec, w, N, h->gm_partial);
+    h2::k_multidot<<<h2::dot_grid(nvec), h2::kDotThreads, 0, s>>>(V, ldv, nvec, w, N, h->gm_partial);
     h2::k_reduce_partials<<<nblocks(nvec, 128), 128, 0, s>>>(h->gm_partial, h2::kDotBlocks, nvec, h->gm_h);
     H2_CUDA(cudaMemcpyAsync(out, h->gm_h, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaStreamSynchronize(s));
@@ -1015,6 +1059,8 @@ extern "C" int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale
         return fail(H2_E_NO_DEVICE, "handle was built host-only");
     if (h_res && (h_res->host.tree.N != h->host.tree.N || h_res->device != h->device))
         return fail(H2_E_INVALID_ARG, "the residual handle has another N or device");
+    if (h->server || (h_res && h_res->server))
+        return fail(H2_E_INVALID_ARG, "handle is in use by a solve server");
     if (!(rtol > 0.0 && rtol < 1.0)) return fail(H2_E_INVALID_ARG, "rtol must be in (0, 1)");
     if (restart < 1 || restart > 1000 || maxit < 1) return fail(H2_E_INVALID_ARG, "restart or maxit out of range");
     if (!std::isfinite(shift) || !std::isfinite(scale)) return fail(H2_E_INVALID_ARG, "shift / scale not finite");
@@ -1062,6 +1108,7 @@ extern "C" int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale
         double* dx = h->gm_d;
         H2_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         double rn = bnorm;
+        bool fallback = false;
         for (int outer = 0; outer < 30; ++outer) {
             if (rn <= rtol * bnorm) { conv = true; break; }
             if (iters >= maxit) break;
@@ -1075,12 +1122,39 @@ extern "C" int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale
             H2_TRY(gm_apply(h_res, shift, scale, x, r, s));
             mv_res++;
             h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(1.0, b, -1.0, r, N);
-            H2_TRY(gm_norm(h, r, &rn, s));
+            double rn_new = 0.0;
+            H2_TRY(gm_norm(h, r, &rn_new, s));
             S.refinements++;
             est = e2;
+            if (rn_new > rtol * bnorm && rn_new > 0.5 * rn) {
+                // the correction did not halve the fp64 residual: undo it
+                h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(-1.0, dx, 1.0, x, N);
+                fallback = true;
+                break;
+            }
+            rn = rn_new;
         }
-        if (rn <= rtol * bnorm) conv = true;
+        if (fallback && iters < maxit) {
+            // finish with fp64 GMRES on the residual handle from the last good x
+            H2_TRY(gm_workspace(h_res, restart));
+            const bool saved_res_profile = h_res->profile;
+            h_res->profile = false;
+            int64_t mv2 = 0;
+            int rc = gm_solve(h_res, shift, scale, b, bnorm, x, rtol, restart, maxit - iters, s,
+                              &iters, &restarts, &mv2, &est, &conv);
+            h_res->profile = saved_res_profile;
+            mv_res += mv2;
+            if (rc != H2_OK) return rc;
+        }
+        if (fallback) {
+            H2_TRY(gm_apply(h_res, shift, scale, x, r, s));
+            mv_res++;
+            h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(1.0, b, -1.0, r, N);
+            H2_TRY(gm_norm(h, r, &rn, s));
+        }
+        conv = rn <= rtol * bnorm;
         S.rel_residual = rn / bnorm;
+        S.fallback = fallback ? 1 : 0;
     }
     H2_CUDA(cudaStreamSynchronize(s));
     S.converged = conv ? 1 : 0;
@@ -1467,9 +1541,12 @@ struct Req {
     double t_submit = 0, t_admit = 0, t_done = 0;
     size_t ws_off = 0, ws_len = 0;         // workspace slice (doubles) of the pool
     double *V = nullptr, *w = nullptr, *x = nullptr, *b = nullptr, *part = nullptr, *hd = nullptr;
+    double* xp = nullptr;                  // iterate before the current cycle (refinement)
     double* hv = nullptr;                  // pinned host projections (m + 1)
     int state = RQ_RESIDUAL, j = 0, iters = 0, restarts = 0;
-    double beta = 0, bnorm = 0, est = 1, relres = 1;
+    int op = 0;                            // 0 inner operator, 1 residual operator by the
+                                           // admission rule, 2 after a fallback
+    double beta = 0, beta_prev = 0, bnorm = 0, est = 1, relres = 1;
     bool done = false, converged = false, xzero = true;
     std::vector<double> H, cs, sn, gv, h1;
 };
@@ -1481,10 +1558,13 @@ double now_s() {
 }  // namespace
 
 struct h2_server_s {
-    std::vector<h2_handle> geoms;
+    std::vector<h2_handle> geoms;          // operators of the Arnoldi products
+    std::vector<h2_handle> res;            // operators of the residuals (geoms[g] or fp64)
+    std::vector<double> floor;             // per geometry: cycle reduction floor (0: plain)
+    std::vector<double> delta;             // per geometry: ||(K_inner - K_res) v|| / ||v||
     std::vector<cudaStream_t> streams;
     std::vector<double*> Xg, Yg;           // per geometry: N x max_active staging
-    int m = 50, max_active = 16;
+    int m = 50, max_active = 16, inner_policy = 0;
     double* pool = nullptr;
     size_t pool_len = 0;                   // doubles
     std::map<size_t, size_t> free_list;    // offset -> length (doubles)
@@ -1501,6 +1581,16 @@ struct h2_server_s {
     std::string worker_error;
     h2_server_stats stats = {};           // admission counters (under mu)
     std::atomic<int64_t> ticks{0}, products{0}, product_columns{0};
+
+    ~h2_server_s() {
+        for (cudaStream_t st : streams) cudaStreamDestroy(st);
+        for (double* p : Xg) cudaFree(p);
+        for (double* p : Yg) cudaFree(p);
+        if (pool) cudaFree(pool);
+        if (pinned) cudaFreeHost(pinned);
+        for (h2_handle h : geoms) if (h->server == this) h->server = nullptr;
+        for (h2_handle h : res) if (h->server == this) h->server = nullptr;
+    }
 };
 
 namespace {
@@ -1537,23 +1627,27 @@ void ws_free(h2_server S, size_t off, size_t n) {
 
 size_t req_doubles(h2_server S, int64_t N) {
     const size_t m = size_t(S->m);
-    return size_t(N) * (m + 1) + 3 * size_t(N) + size_t(h2::kDotBlocks) * (m + 1) + (m + 1);
+    return size_t(N) * (m + 1) + 4 * size_t(N) + size_t(h2::kDotBlocks) * (m + 1) + (m + 1);
 }
 
-// y = A x for every request in rs (all on geometry g): one multi-RHS product.
-int serve_products(h2_server S, int g, const std::vector<std::pair<Req*, const double*>>& rs) {
-    h2_handle h = S->geoms[g];
+int matvec_any(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k,
+               cudaStream_t st) {
+    const int stor = h->host.storage;
+    return (stor == H2_F64)   ? matvec_one<h2::F64>(h, X, ldx, Y, ldy, k, st)
+           : (stor == H2_F32) ? matvec_one<h2::F32>(h, X, ldx, Y, ldy, k, st)
+                              : matvec_one<h2::DF>(h, X, ldx, Y, ldy, k, st);
+}
+
+// y = A x for every request in rs (all on geometry g, operator h): one
+// multi-RHS product.
+int serve_products(h2_server S, int g, h2_handle h, const std::vector<std::pair<Req*, const double*>>& rs) {
     cudaStream_t st = S->streams[g];
     const int64_t N = h->host.tree.N;
     const int k = int(rs.size());
     for (int c = 0; c < k; ++c)
         H2_CUDA(cudaMemcpyAsync(S->Xg[g] + int64_t(c) * N, rs[c].second, sizeof(double) * N,
                                 cudaMemcpyDeviceToDevice, st));
-    const int stor = h->host.storage;
-    int rc = (stor == H2_F64)   ? matvec_one<h2::F64>(h, S->Xg[g], N, S->Yg[g], N, k, st)
-             : (stor == H2_F32) ? matvec_one<h2::F32>(h, S->Xg[g], N, S->Yg[g], N, k, st)
-                                : matvec_one<h2::DF>(h, S->Xg[g], N, S->Yg[g], N, k, st);
-    if (rc != H2_OK) return rc;
+    H2_TRY(matvec_any(h, S->Xg[g], N, S->Yg[g], N, k, st));
     for (int c = 0; c < k; ++c) {
         Req* r = rs[c].first;
         // w = shift x + scale K~ x
@@ -1567,7 +1661,7 @@ int serve_products(h2_server S, int g, const std::vector<std::pair<Req*, const d
 
 void dots_async(h2_server S, Req* r, const double* Vm, int nvec, const double* w, cudaStream_t st) {
     const int64_t N = S->geoms[r->g]->host.tree.N;
-    h2::k_multidot<<<h2::kDotBlocks, h2::kDotThreads, 0, st>>>(Vm, N, nvec, w, N, r->part);
+    h2::k_multidot<<<h2::dot_grid(nvec), h2::kDotThreads, 0, st>>>(Vm, N, nvec, w, N, r->part);
     h2::k_reduce_partials<<<nblocks(nvec, 128), 128, 0, st>>>(r->part, h2::kDotBlocks, nvec, r->hd);
     cudaMemcpyAsync(r->hv, r->hd, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st);
 }
@@ -1581,7 +1675,8 @@ int sync_all(h2_server S) {
 int serve_tick(h2_server S, std::vector<Req*>& act) {
     const int m = S->m;
     // phase A: products (residual b - A x, or the next Arnoldi vector)
-    std::map<int, std::vector<std::pair<Req*, const double*>>> by_g;
+    // key (g, 0): residual products on res[g]; (g, 1): Arnoldi products on geoms[g]
+    std::map<std::pair<int, int>, std::vector<std::pair<Req*, const double*>>> by_g;
     for (Req* r : act) {
         const int64_t N = S->geoms[r->g]->host.tree.N;
         if (r->state == RQ_RESIDUAL) {
@@ -1589,12 +1684,15 @@ int serve_tick(h2_server S, std::vector<Req*>& act) {
                 H2_CUDA(cudaMemsetAsync(r->w, 0, sizeof(double) * N, S->streams[r->g]));
                 continue;
             }
-            by_g[r->g].push_back({r, r->x});
+            by_g[{r->g, 0}].push_back({r, r->x});
         } else {
-            by_g[r->g].push_back({r, r->V + int64_t(r->j) * N});
+            by_g[{r->g, r->op == 0 ? 1 : 0}].push_back({r, r->V + int64_t(r->j) * N});
         }
     }
-    for (auto& kv : by_g) H2_TRY(serve_products(S, kv.first, kv.second));
+    for (auto& kv : by_g) {
+        const int g = kv.first.first;
+        H2_TRY(serve_products(S, g, kv.first.second ? S->geoms[g] : S->res[g], kv.second));
+    }
     // phase B: first projections / residual norms
     for (Req* r : act) {
         const int64_t N = S->geoms[r->g]->host.tree.N;
@@ -1618,6 +1716,18 @@ int serve_tick(h2_server S, std::vector<Req*>& act) {
                 r->converged = r->beta <= r->rtol * r->bnorm;
                 r->done = true;
                 continue;
+            }
+            const bool refine = S->floor[r->g] > 0.0 && r->op == 0;
+            if (refine && !r->xzero && r->beta > 0.5 * r->beta_prev) {
+                // the last cycle on the inner operator did not halve the fp64
+                // residual: undo it and continue on the residual operator
+                H2_CUDA(cudaMemcpyAsync(r->x, r->xp, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+                r->op = 2;
+                continue;                          // residual again next tick
+            }
+            if (refine) {
+                H2_CUDA(cudaMemcpyAsync(r->xp, r->x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+                r->beta_prev = r->beta;
             }
             if (!r->xzero) r->restarts++;
             h2::k_axpby<<<nblocks(N, 256), 256, 0, st>>>(0.0, r->V, 1.0 / r->beta, r->V, N);
@@ -1668,7 +1778,11 @@ int serve_tick(h2_server S, std::vector<Req*>& act) {
         r->gv[j] = r->cs[j] * r->gv[j];
         r->iters++;
         r->est = std::fabs(r->gv[j + 1]) / r->bnorm;
-        const bool stop_cycle = r->est <= r->rtol || j + 1 == m || r->iters >= r->maxit || hn == 0.0;
+        // plain: until the estimate meets rtol; refinement: until this cycle's
+        // residual has dropped to the inner operator's precision (or to rtol)
+        const double fl = r->op == 0 ? S->floor[r->g] : 0.0;
+        const double thr = fl > 0.0 ? std::max(fl * r->beta, 0.5 * r->rtol * r->bnorm) : r->rtol * r->bnorm;
+        const bool stop_cycle = std::fabs(r->gv[j + 1]) <= thr || j + 1 == m || r->iters >= r->maxit || hn == 0.0;
         if (!stop_cycle) {
             r->j = j + 1;
             continue;
@@ -1710,7 +1824,8 @@ void serve_loop(h2_server S) {
                 r->w = base + N * (S->m + 1);
                 r->x = r->w + N;
                 r->b = r->x + N;
-                r->part = r->b + N;
+                r->xp = r->b + N;
+                r->part = r->xp + N;
                 r->hd = r->part + size_t(h2::kDotBlocks) * (S->m + 1);
                 const int slot = S->pinned_free.back();
                 S->pinned_free.pop_back();
@@ -1727,6 +1842,11 @@ void serve_loop(h2_server S) {
                 cudaStream_t st = S->streams[r->g];
                 cudaMemcpyAsync(r->b, r->f.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st);
                 cudaMemsetAsync(r->x, 0, sizeof(double) * N, st);
+                // the inner operator serves this request if its measured error is
+                // small against the shift (below 1/10 of the smallest eigenvalue
+                // bound |shift| of shift I + scale K for positive semi-definite K)
+                r->op = (S->floor[r->g] == 0.0 || S->inner_policy == 1 || r->shift == 0.0 ||
+                         S->delta[r->g] * std::fabs(r->scale) <= 0.1 * std::fabs(r->shift)) ? 0 : 1;
                 S->stats.admitted++;
             }
             S->stats.max_active = std::max<int64_t>(S->stats.max_active, int64_t(S->active.size()));
@@ -1776,8 +1896,8 @@ void serve_loop(h2_server S) {
 
 }  // namespace
 
-extern "C" int h2_server_create(const h2_handle* geoms, int ngeom, const h2_server_opts* opts,
-                                h2_server* out) {
+extern "C" int h2_server_create(const h2_handle* geoms, const h2_handle* res_geoms, int ngeom,
+                                const h2_server_opts* opts, h2_server* out) {
     g_err.clear();
     if (!geoms || ngeom < 1 || !out) return fail(H2_E_INVALID_ARG, "NULL argument or no geometry");
     *out = nullptr;
@@ -1788,11 +1908,22 @@ extern "C" int h2_server_create(const h2_handle* geoms, int ngeom, const h2_serv
     S->m = o.restart > 0 ? o.restart : 50;
     S->max_active = o.max_active > 0 ? o.max_active : 16;
     if (S->m > 1000 || S->max_active > 1024) return fail(H2_E_INVALID_ARG, "restart or max_active too large");
+    if (o.inner_policy < 0 || o.inner_policy > 1) return fail(H2_E_INVALID_ARG, "unknown inner_policy");
+    S->inner_policy = o.inner_policy;
     int64_t maxN = 0;
     for (int g = 0; g < ngeom; ++g) {
         if (!geoms[g] || !geoms[g]->on_device) return fail(H2_E_INVALID_ARG, "geometry handle not on the device");
         if (geoms[g]->device != geoms[0]->device) return fail(H2_E_INVALID_ARG, "geometries on different devices");
+        h2_handle rh = res_geoms ? res_geoms[g] : geoms[g];
+        if (!rh || !rh->on_device) return fail(H2_E_INVALID_ARG, "residual handle not on the device");
+        if (rh->device != geoms[g]->device || rh->host.tree.N != geoms[g]->host.tree.N ||
+            rh->host.tree.perm != geoms[g]->host.tree.perm)
+            return fail(H2_E_INVALID_ARG, "residual handle of another geometry");
+        if (geoms[g]->server || rh->server)
+            return fail(H2_E_INVALID_ARG, "a handle is in use by another solve server");
         S->geoms.push_back(geoms[g]);
+        S->res.push_back(rh);
+        S->floor.push_back(rh == geoms[g] ? 0.0 : (geoms[g]->host.storage == H2_F32 ? 1e-5 : 1e-10));
         maxN = std::max(maxN, geoms[g]->host.tree.N);
     }
     const size_t budget = o.workspace_bytes > 0 ? size_t(o.workspace_bytes)
@@ -1821,8 +1952,48 @@ extern "C" int h2_server_create(const h2_handle* geoms, int ngeom, const h2_serv
         int rc = grow_vec(geoms[g], S->max_active);
         if (rc != H2_OK) return rc;
         geoms[g]->profile = false;
+        double delta = 0.0;
+        if (S->res[g] != geoms[g]) {
+            rc = grow_vec(S->res[g], S->max_active);
+            if (rc != H2_OK) return rc;
+            S->res[g]->profile = false;
+            // error of the inner operator on one seeded N(0, 1) vector
+            std::vector<double> v(static_cast<size_t>(N)), ya(static_cast<size_t>(N)), yb(static_cast<size_t>(N));
+            std::mt19937_64 gen(0x5eed + uint64_t(g));
+            std::normal_distribution<double> nd(0.0, 1.0);
+            for (auto& a : v) a = nd(gen);
+            H2_CUDA(cudaMemcpyAsync(x, v.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
+            H2_TRY(matvec_any(geoms[g], x, N, y, N, 1, st));
+            H2_CUDA(cudaMemcpyAsync(ya.data(), y, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+            H2_TRY(matvec_any(S->res[g], x, N, y, N, 1, st));
+            H2_CUDA(cudaMemcpyAsync(yb.data(), y, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+            H2_CUDA(cudaStreamSynchronize(st));
+            double dn = 0.0, vn = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                dn += (ya[i] - yb[i]) * (ya[i] - yb[i]);
+                vn += v[i] * v[i];
+            }
+            delta = std::sqrt(dn / vn);
+        }
+        S->delta.push_back(delta);
     }
     S->stats.workspace_bytes = int64_t(S->pool_len * sizeof(double));
+    {
+        // every handle serves one geometry slot: products of different slots run
+        // concurrently and each handle has one coefficient buffer
+        std::map<h2_handle, int> slot;
+        for (int g = 0; g < ngeom; ++g)
+            for (h2_handle hh : {S->geoms[g], S->res[g]}) {
+                auto it = slot.find(hh);
+                if (it != slot.end() && it->second != g)
+                    return fail(H2_E_INVALID_ARG, "one handle appears in two geometry slots");
+                slot[hh] = g;
+            }
+    }
+    for (int g = 0; g < ngeom; ++g) {
+        S->geoms[g]->server = S.get();
+        S->res[g]->server = S.get();
+    }
     h2_server_s* raw = S.get();
     S->worker = std::thread([raw] { serve_loop(raw); });
     *out = S.release();
@@ -1879,6 +2050,7 @@ extern "C" int h2_server_wait(h2_server S, int64_t ticket, double* x, h2_request
         st->converged = r->converged ? 1 : 0;
         st->iterations = r->iters;
         st->restarts = r->restarts;
+        st->op = r->op;
         st->rel_residual = r->relres;
         st->queue_seconds = r->t_admit - r->t_submit;
         st->latency_seconds = r->t_done - r->t_submit;
@@ -1911,11 +2083,6 @@ extern "C" void h2_server_destroy(h2_server S) {
     if (S->worker.joinable()) S->worker.join();
     cudaDeviceSynchronize();
     for (auto& kv : S->reqs) delete kv.second;
-    for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
-    for (double* p : S->Xg) cudaFree(p);
-    for (double* p : S->Yg) cudaFree(p);
-    if (S->pool) cudaFree(S->pool);
-    if (S->pinned) cudaFreeHost(S->pinned);
-    delete S;
+    delete S;   // the destructor frees streams and buffers and releases the handles
 }
 

@@ -8,31 +8,30 @@
 
 namespace h2 {
 
-constexpr int kDotBlocks = 304;      // 2 x 152 SMs
-constexpr int kDotThreads = 256;
+constexpr int kDotBlocks = 304;      // 2 x 152 SMs: row slices
+constexpr int kDotThreads = 256;     // 8 warps, one vector each
+constexpr int kDotWarps = kDotThreads / 32;
 
-// partial[b * nvec + i] = sum over block b's slice of V[:, i] . w
+inline dim3 dot_grid(int nvec) { return dim3(kDotBlocks, unsigned((nvec + kDotWarps - 1) / kDotWarps)); }
+
+// partial[b * nvec + v] = sum over row slice b of V[:, v] . w.  Grid
+// dot_grid(nvec): block (b, y) covers slice b for vectors 8 y .. 8 y + 7, one
+// warp per vector (lanes stride the slice, then a shuffle reduction), so long
+// Krylov bases need no block-wide barrier per vector.
 __global__ void k_multidot(const double* __restrict__ V, int64_t ldv, int nvec,
                            const double* __restrict__ w, int64_t N,
                            double* __restrict__ partial) {
-    __shared__ double red[kDotThreads / 32];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int v = int(blockIdx.y) * kDotWarps + warp;
+    if (v >= nvec) return;
     const int64_t per = (N + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = int64_t(blockIdx.x) * per, i1 = min(N, i0 + per);
-    for (int v = 0; v < nvec; ++v) {
-        const double* col = V + int64_t(v) * ldv;
-        double s = 0.0;
-        for (int64_t k = i0 + threadIdx.x; k < i1; k += blockDim.x) s = fma(col[k], w[k], s);
+    const double* col = V + int64_t(v) * ldv;
+    double s = 0.0;
+    for (int64_t k = i0 + lane; k < i1; k += 32) s = fma(col[k], w[k], s);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int k = 0; k < int(blockDim.x / 32); ++k) t += red[k];
-            partial[int64_t(blockIdx.x) * nvec + v] = t;
-        }
-        __syncthreads();
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) partial[int64_t(blockIdx.x) * nvec + v] = s;
 }
 
 // out[i] = sum_b partial[b * nvec + i], b in order

@@ -63,3 +63,29 @@ def batched_instances(count=512, seed0=3000):
                         nrhs=r))
     return out
 
+
+
+def served_geometries(count=4, seed0=4000, n_max_3d=32768):
+    """Geometries of the served-solves workload: geometry k has points uniform
+    in [-1, 1]^d (d = 2 for even k, 3 for odd k) with N = floor(exp(U[ln 4096,
+    ln N_hi])), N_hi = 2^20 in 2D and n_max_3d in 3D, and the right-hand side
+    f(x) = sin(3 x_1) cos(2 x_2) at the points; streams seeded with 4000 + k."""
+    out = []
+    for k in range(count):
+        rng = np.random.Generator(np.random.PCG64(seed0 + k))
+        d = 2 if k % 2 == 0 else 3
+        hi = 2 ** 20 if d == 2 else n_max_3d
+        N = int(np.floor(np.exp(rng.uniform(np.log(4096), np.log(hi)))))
+        P = rng.uniform(-1.0, 1.0, size=(N, d))
+        f = np.sin(3.0 * P[:, 0]) * np.cos(2.0 * P[:, 1])
+        out.append(dict(k=k, N=N, d=d, points=P, f=f))
+    return out
+
+
+def poisson_arrivals(count, rate, ngeom, seed=4999):
+    """Request stream: arrival times (s) of a Poisson process of the given rate
+    and the geometry each request targets (uniform)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    g = rng.integers(0, ngeom, size=count)
+    return t - t[0], g

@@ -69,6 +69,33 @@ def test_unsupported_combinations_are_rejected():
     assert e.value.code == -5
 
 
+def test_convert_rejects_before_touching_a_device():
+    P = inputs.points(300, 2, 2)
+    fly = H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, near="fly", host_only=True)
+    with pytest.raises(H2Error) as e:
+        fly.convert("df64")                       # double-float needs stored near blocks
+    assert e.value.code == -5
+    hp = H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, variant="h2plush", host_only=True)
+    with pytest.raises(H2Error) as e:
+        hp.convert("df64")
+    assert e.value.code == -5
+    h = ctypes.c_void_p()
+    assert pkg.lib().h2_convert(fly._h, 7, ctypes.byref(h)) == -1
+    assert pkg.lib().h2_convert(None, 0, ctypes.byref(h)) == -1
+    if not _has_gpu():
+        with pytest.raises(H2Error) as e:
+            fly.convert("f32")
+        assert e.value.code == -6
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
 def test_near_field_storage_accounting():
     P = inputs.points(4096, 2, 1001)
     S = H2Matrix(P, "log2d", leaf_size=64, tol=1e-6, host_only=True).info()

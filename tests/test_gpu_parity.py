@@ -213,3 +213,19 @@ def test_c2_3d_invr_n262144_sampled_rows(storage):
     re_orc = dense.relative_error(ref, exact)
     print(f"c2 {storage}: RE gpu {re_gpu:.4e} oracle {re_orc:.4e}")
     assert re_gpu <= max(10 * 1e-6, 1.02 * re_orc)
+
+
+@pytest.mark.parametrize("src_near,target,direct_near", [(None, "f32", "stored"),
+                                                        (None, "df64", None),
+                                                        ("fly", "f64", "fly")])
+def test_converted_handle_equals_a_direct_build(src_near, target, direct_near):
+    """h2_convert re-uploads the packed operators of one construction in another
+    storage: its products equal a handle built directly with that storage."""
+    P = inputs.points(6000, 2, 21)
+    q = torch.tensor(inputs.rhs(6000, 1, 22), device="cuda:0")
+    src_storage = "f32" if src_near == "fly" else "f64"
+    A = H2Matrix(P, "log2d", leaf_size=32, tol=1e-8, storage=src_storage, near=src_near)
+    C = A.convert(target)
+    D = H2Matrix(P, "log2d", leaf_size=32, tol=1e-8, storage=target, near=direct_near)
+    assert C.info()["near_stored"] == D.info()["near_stored"]
+    assert np.array_equal(C.matvec(q).cpu().numpy(), D.matvec(q).cpu().numpy())

@@ -1,5 +1,7 @@
 """The continuous-batching solve server: results alone and in the mix,
-admission by the workspace budget, and agreement with h2_gmres."""
+admission by the workspace budget, agreement with h2_gmres, and
+mixed-precision serving (fp32 operators, fp64 residuals) reaching the fp64
+tolerance."""
 
 import threading
 
@@ -65,7 +67,7 @@ def test_admission_respects_the_workspace_budget_and_matches_gmres():
     G = _geoms()
     mats = [m for _, m in G]
     N = max(m.N for m in mats)
-    per = ((100 + 1) + 3) * N * 8 + 304 * 101 * 8 + 101 * 8
+    per = ((100 + 1) + 4) * N * 8 + 304 * 101 * 8 + 101 * 8
     S = H2Server(mats, workspace_bytes=2 * per + 1024, restart=100, max_active=8)
     ts = [S.submit(2, _rhs(G[2][0]), shift=1e-2, rtol=1e-8, maxit=3000) for _ in range(5)]
     xs = [S.wait(t)[0][:mats[2].N] for t in ts]
@@ -77,3 +79,65 @@ def test_admission_respects_the_workspace_budget_and_matches_gmres():
     ref = x.cpu().numpy()
     for xs_ in xs:
         assert np.linalg.norm(xs_ - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def _true_residual(A, x, f, shift):
+    """||f - (shift x + K~ x)|| / ||f|| with the fp64 product, computed here."""
+    xt = torch.tensor(x, device="cuda:0")
+    r = torch.tensor(f, device="cuda:0") - (shift * xt + A.matvec(xt))
+    return float(torch.linalg.norm(r) / np.linalg.norm(f))
+
+
+def test_mixed_precision_server_reaches_the_fp64_tolerance():
+    G = _geoms()
+    mats = [m for _, m in G]
+    lows = [m.convert("f32") for m in mats]
+    jobs = [(k % 3, 1e-2 * (1 + k % 2)) for k in range(6)]
+    # one server at a time: a server owns its handles (the fp64 ones serve both)
+    plain = H2Server(mats, restart=100, max_active=8)
+    tp = [plain.submit(g, _rhs(G[g][0]), shift=s, rtol=1e-8, maxit=6000) for g, s in jobs]
+    outp = [plain.wait(t) for t in tp]
+    with pytest.raises(Exception):
+        H2Server(lows, residual=mats)             # the fp64 handles are taken
+    plain.close()
+    mixed = H2Server(lows, residual=mats, restart=100, max_active=8)
+    tm = [mixed.submit(g, _rhs(G[g][0]), shift=s, rtol=1e-8, maxit=6000) for g, s in jobs]
+    outm = [mixed.wait(t) for t in tm]
+    mixed.close()
+    for (g, s), (xp, sp), (xm, sm) in zip(jobs, outp, outm):
+        N = mats[g].N
+        xp, xm = xp[:N], xm[:N]
+        assert sp["converged"] == 1 and sm["converged"] == 1, (sp, sm)
+        assert sm["rel_residual"] <= 1e-8
+        assert _true_residual(mats[g], xm, _rhs(G[g][0]), s) <= 1.01e-8
+        assert np.linalg.norm(xm - xp) / np.linalg.norm(xp) <= 1e-5
+        assert sm["restarts"] >= 1            # at least one fp64 refinement step
+        assert sm["op"] in (0, 2)             # fp32 passes the admission rule here
+
+
+def test_precision_guards_route_requests_to_the_fp64_operator():
+    """An inner operator far from the residual operator (IMQ with c = 0.5 against
+    c = 0.1, same points) fails the admission rule (op 1); forced onto it, the
+    first cycle does not halve the fp64 residual and is undone (op 2); an fp32
+    copy passes (op 0).  Every request still reaches the fp64 tolerance."""
+    P = inputs.points(3000, 2, 900)
+    f = _rhs(P)
+    A = H2Matrix(P, "imq", leaf_size=64, tol=1e-8, kparam=0.1)
+    W = H2Matrix(P, "imq", leaf_size=64, tol=1e-8, kparam=0.5)
+    L = A.convert("f32")
+    cases = [(W, 0, 1), (W, 1, 2), (L, 0, 0)]     # (inner, inner_policy, expected op)
+    for inner, policy, op in cases:
+        S = H2Server([inner], residual=[A], restart=100, max_active=4, inner_policy=policy)
+        with pytest.raises(Exception):
+            A.matvec(torch.zeros(3000, dtype=torch.float64, device="cuda:0"))  # served handle
+        x, st = S.wait(S.submit(0, f, shift=1.0, rtol=1e-8, maxit=3000))
+        S.close()
+        assert st["converged"] == 1 and st["op"] == op, st
+        assert _true_residual(A, x[:3000], f, 1.0) <= 1.01e-8
+    # h2_gmres: the same guard finishes the solve with fp64 GMRES
+    b = torch.tensor(f, device="cuda:0")
+    x, st = W.gmres(b, shift=1.0, rtol=1e-8, restart=100, maxit=3000, residual=A)
+    assert st["converged"] == 1 and st["fallback"] == 1, st
+    assert _true_residual(A, x.cpu().numpy(), f, 1.0) <= 1.01e-8
+    x, st = L.gmres(b, shift=1.0, rtol=1e-8, restart=100, maxit=3000, residual=A)
+    assert st["converged"] == 1 and st["fallback"] == 0, st
