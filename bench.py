@@ -149,7 +149,9 @@ def bench_ours(args, rank, world):
     N, nrhs = w["N"], w["nrhs"]
     t0 = time.perf_counter()
     A = H2Matrix(w["points"], w["kernel"], leaf_size=w["n_max"], tol=w["eps"],
-                 variant=args.variant, storage=args.storage)
+                 variant=args.variant, storage=args.storage,
+                 tensor_cores=bool(args.tensor_cores) and args.storage == "f32",
+                 near="stored" if args.tensor_cores else None)
     build_s = time.perf_counter() - t0
     info = A.info()
     q = torch.tensor(w["q"].reshape(N, nrhs), dtype=torch.float64, device=dev)
@@ -225,19 +227,23 @@ def bench_ours(args, rank, world):
     # roofline of the dominant kernel (stage timed with CUDA events)
     per = {k: v / max(calls, 1) for k, v in stages.items()}
     dom = max(per, key=per.get)
-    ts = {"f64": 8, "df64": 8, "f32": 4}[args.storage]
+    # coefficient bytes (fp64, float pairs, float, float); operator entry bytes
+    # are already in the stored-byte counts of h2_info
+    vs = {"f64": 8, "df64": 8, "f32": 4, "bf16": 4}[args.storage]
     hbm, how = _peaks()
     roof = {"kernel": dom, "stage_ms": {k: round(v, 4) for k, v in per.items()},
             "profiled_ms_per_step": round(prof_ms_step, 4)}
     if dom == "m2l" or (dom == "leaf" and info["near_stored"]):
+        # operators once per product, coefficients once per right-hand side
         if dom == "m2l":
-            alg = info["bytes_m2l"] + (info["m2l_src_coeffs"] + info["m2l_dst_coeffs"]) * ts
+            alg = info["bytes_m2l"] + (info["m2l_src_coeffs"] + info["m2l_dst_coeffs"]) * vs * nrhs
         else:
-            alg = info["bytes_leaf_rows"] + (info["leaf_src_coeffs"] + N) * ts
+            alg = info["bytes_leaf_rows"] + (info["leaf_src_coeffs"] + N) * vs * nrhs
         sec = per[dom] / 1e3
         ach = alg / sec / 1e9
         traffic = None
-        if dom == "m2l" and args.variant == "h2star" and args.storage in M2L_TRAFFIC_RATIO:
+        if (dom == "m2l" and args.variant == "h2star" and args.storage in M2L_TRAFFIC_RATIO
+                and nrhs == 1):
             traffic = int(M2L_TRAFFIC_RATIO[args.storage] * alg)
         roof.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s",
                     frac=round(ach / hbm, 4), traffic=traffic, alg_bytes=alg,
@@ -263,12 +269,13 @@ def bench_ours(args, rank, world):
         "config": {"workload": args.workload, "N": N, "d": w["d"],
                    "kernel": KERNEL_NAMES[w["kernel"]], "leaf_size": w["n_max"],
                    "kappa": info["kappa"], "eps": w["eps"], "variant": VARIANT_NAMES[args.variant],
-                   "storage": args.storage, "nrhs": nrhs,
+                   "storage": args.storage, "nrhs": nrhs, "tensor_cores": bool(args.tensor_cores) or args.storage == "bf16",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "operators larger than L2 (no flush)",
                    "build_seconds": round(build_s, 2),
                    "device_bytes": info["bytes_device"],
                    "autotuned_rows_per_warp": {"m2l": info["rw_m2l"], "leaf": info["rw_leaf"]},
+                   "tc_persistent_ctas": info["tc_blocks"], "tc_occupancy_api": info["tc_occupancy"],
                    "ranks": info["ranks"]},
         "clocks": clk,
         "e2e": {"value": world * N * nrhs / (e2e_ms / 1e3), "unit": UNIT,
@@ -512,7 +519,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2_3d_invr_n262144")
-    ap.add_argument("--storage", default="f64", choices=["f64", "df64", "f32"])
+    ap.add_argument("--storage", default="f64", choices=["f64", "df64", "f32", "bf16"])
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="fp32 storage: RHS tiles of 16-64 columns on tcgen05 (tf32)")
     ap.add_argument("--variant", default="h2star", choices=list(VARIANT_NAMES))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--gmres-solves", type=int, default=10)

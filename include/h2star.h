@@ -59,13 +59,18 @@ extern "C" {
                                      kept as a pair of floats (hi + lo, 48-bit significand) and
                                      multiplied / accumulated with error-free transformations
                                      on the FP32 pipe (near field from stored blocks)           */
+#define H2_BF16               3   /* operators and near-field blocks stored in bfloat16, fp32
+                                     coefficients; RHS tiles of 16-64 columns run on the tensor
+                                     cores (tcgen05, bf16 x bf16 -> fp32 accumulate: the
+                                     coefficients are rounded to bf16 as MMA inputs), narrower
+                                     tiles on the CUDA cores (fp32 multiply-add)             */
 
 /* Optional build settings; pass NULL for all defaults.  Zero-initialise and
  * set the fields you need: every zero field means "default". */
 typedef struct {
     double eps_far;        /* NCA tolerance for the far field (default: tol)           */
     double eps_ver;        /* tolerance for vertex-sharing clusters (default: tol)     */
-    int    storage;        /* H2_F64 (default) or H2_F32                               */
+    int    storage;        /* H2_F64 (default), H2_F32, H2_DF64 or H2_BF16             */
     int    kappa;          /* leaf level; 0 = smallest kappa with leaf_size 2^(d kappa) >= N
                               (§3.1); a positive value forces that depth           */
     int    use_domain;     /* 1: use domain_lo / domain_side as the root hyper-cube C  */
@@ -79,6 +84,9 @@ typedef struct {
     int    near_mode;      /* near field: 0 default (stored blocks for H2_F64 / H2_DF64,
                               on the fly from the coordinates for H2_F32), 1 on the fly,
                               2 stored kernel blocks (with L2P fused into them)       */
+    int    tensor_cores;   /* H2_F32 only: 1 = RHS tiles of 16-64 columns run on the
+                              tensor cores in tf32 (10-bit significand multiplies,
+                              fp32 accumulate); 0 (default) = fp32 CUDA-core FMA     */
 } h2_build_opts;
 
 typedef struct h2_handle_s* h2_handle;
@@ -167,6 +175,9 @@ typedef struct {
     int64_t bytes_device;          /* total device bytes held by the handle                */
     int64_t alg_bytes_per_rhs;     /* algorithmic HBM bytes of one MVP with one RHS      */
     double  build_seconds;         /* host construction wall time                          */
+    int     tc_blocks[3];          /* tensor-core products: persistent CTAs per launch for
+                                      RHS tiles of 64 / 32 / 16 (0: no tensor cores)     */
+    int     tc_occupancy[3];       /* the runtime's resident-CTA estimate per SM (report) */
 } h2_stats;
 
 /* h2_info -- fill *st (host).  Errors: H2_E_INVALID_ARG. */

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libh2star.so")
 
 KERNELS = {"log2d": 0, "invr": 1, "imq": 2, "matern12": 3}
 VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2}
-STORAGE = {"f64": 0, "f32": 1, "df64": 2}
+STORAGE = {"f64": 0, "f32": 1, "df64": 2, "bf16": 3}
 NEAR = {None: 0, "fly": 1, "stored": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
 EXPORTED = ("h2_build", "h2_convert", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
@@ -36,7 +36,7 @@ class BuildOpts(ctypes.Structure):
                 ("use_domain", ctypes.c_int), ("domain_lo", ctypes.c_double * 3),
                 ("domain_side", ctypes.c_double), ("threads", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("kparam", ctypes.c_double),
-                ("near_mode", ctypes.c_int)]
+                ("near_mode", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("near_stored", ctypes.c_int), ("rw_m2l", ctypes.c_int), ("rw_leaf", ctypes.c_int),
                 ("bytes_lowrank", ctypes.c_int64),
                 ("bytes_device", ctypes.c_int64), ("alg_bytes_per_rhs", ctypes.c_int64),
-                ("build_seconds", ctypes.c_double)]
+                ("build_seconds", ctypes.c_double), ("tc_blocks", ctypes.c_int * 3),
+                ("tc_occupancy", ctypes.c_int * 3)]
 
 
 class GmresStats(ctypes.Structure):
@@ -159,7 +160,7 @@ class H2Matrix:
 
     def __init__(self, points, kernel, leaf_size=64, tol=1e-8, variant="h2star", storage="f64",
                  eps_far=None, eps_ver=None, kappa=None, domain=None, threads=0,
-                 host_only=False, kparam=None, near=None):
+                 host_only=False, kparam=None, near=None, tensor_cores=False):
         P = np.ascontiguousarray(points, dtype=np.float64)
         if P.ndim != 2:
             raise ValueError("points must be N x d")
@@ -180,6 +181,7 @@ class H2Matrix:
         o.host_only = int(host_only)
         o.kparam = kparam or 0.0
         o.near_mode = NEAR[near]
+        o.tensor_cores = int(tensor_cores)
         h = ctypes.c_void_p()
         _check(lib().h2_build(P.ctypes.data, self.N, self.d, KERNELS[kernel], leaf_size, tol,
                               VARIANTS[variant], ctypes.byref(o), ctypes.byref(h)))
@@ -246,8 +248,11 @@ class H2Matrix:
         st = Stats()
         _check(lib().h2_info(self._h, ctypes.byref(st)))
         out = {f[0]: getattr(st, f[0]) for f in Stats._fields_
-               if f[0] not in ("rank_min", "rank_max", "rank_avg", "m2l_pairs")}
+               if f[0] not in ("rank_min", "rank_max", "rank_avg", "m2l_pairs", "tc_blocks",
+                               "tc_occupancy")}
         out["m2l_pairs"] = list(st.m2l_pairs)
+        out["tc_blocks"] = list(st.tc_blocks)
+        out["tc_occupancy"] = list(st.tc_occupancy)
         out["ranks"] = [{l: (st.rank_min[b][l], round(st.rank_avg[b][l], 2), st.rank_max[b][l])
                          for l in range(st.kappa + 1) if st.rank_max[b][l] > 0}
                         for b in range(st.nbases)]

@@ -25,6 +25,7 @@
 #include "h2_internal.hpp"
 #include "gmres_kernels.cuh"
 #include "mvp_kernels.cuh"
+#include "tc_kernels.cuh"
 
 namespace {
 
@@ -110,6 +111,12 @@ struct h2_handle_s {
     double* gm_partial = nullptr;       // kDotBlocks x (m + 1)
     double* gm_h = nullptr;             // m + 1
     std::vector<void*> gm_allocs;
+    // tensor-core products: device error flag (bounded waits that expired) and
+    // its pinned host copy, refreshed at the end of every product that used them
+    int* tc_err = nullptr;
+    int* tc_err_host = nullptr;
+    int tc_blocks[3] = {0, 0, 0};       // persistent grid for RHS tiles of 64 / 32 / 16
+    int tc_occupancy[3] = {0, 0, 0};    // cudaOccupancy estimate (reported only)
 };
 
 namespace {
@@ -149,6 +156,20 @@ int dev_alloc(h2_handle h, void** dst, size_t bytes) {
 template <class A> struct Conv;
 template <> struct Conv<h2::F64> { static double of(double a) { return a; } };
 template <> struct Conv<h2::F32> { static float of(double a) { return float(a); } };
+// bfloat16 by round-to-nearest-even of the float's upper 16 bits
+template <> struct Conv<h2::BF16> {
+    static __nv_bfloat16 of(double a) {
+        const float f = float(a);
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        uint16_t b;
+        if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) b = 0x7FC0;   // NaN
+        else b = uint16_t((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+        __nv_bfloat16_raw r;
+        r.x = b;
+        return __nv_bfloat16(r);
+    }
+};
 template <> struct Conv<h2::DF> {
     static float2 of(double a) {
         const float hi = float(a);
@@ -216,7 +237,9 @@ void launch_rows_rw(const DevRowTasks& R, const void* ops, void* vec, cudaStream
 // Largest RHS tile: 4 columns in fp32, 2 in fp64 / double-float.  Wider tiles
 // (8, 16) are compiled but lose: with fewer rows per warp every task re-stages
 // its coefficient tile once per 8 rows, so they are not used.
-template <class A> constexpr int max_tile() { return std::is_same<A, h2::F32>::value ? 4 : 2; }
+template <class A> constexpr int max_tile() {
+    return (std::is_same<A, h2::F32>::value || std::is_same<A, h2::BF16>::value) ? 4 : 2;
+}
 
 template <class A>
 void launch_rows(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate,
@@ -247,6 +270,89 @@ std::vector<std::pair<int, int>> rhs_tiles(int nrhs) {
     int c = 0;
     for (int w = max_tile<A>(); w >= 1; w /= 2)
         while (nrhs - c >= w) { t.push_back({c, w}); c += w; }
+    return t;
+}
+
+// Tensor-core block rows: bf16 storage always, fp32 storage when built with
+// tensor_cores; RHS tiles of 64 / 32 / 16 columns.
+template <class A> bool tc_on(h2_handle h) {
+    if constexpr (std::is_same<A, h2::BF16>::value) return true;
+    else if constexpr (std::is_same<A, h2::F32>::value) return h->host.tensor_cores != 0;
+    else return false;
+}
+
+template <typename S, int NT> constexpr int tc_smem() {
+    return 2 * (h2::tc::kATileBytes + NT * h2::tc::kChunkBytes) + 64;
+}
+
+// Resident CTAs per SM from the two budgets that bind: shared memory (the
+// SM's opt-in maximum, 1 KB reserved per CTA) and TMEM (512 columns per SM).
+template <typename S, int NT>
+int tc_setup_nt(h2_handle h, int nsm, int smem_sm, int slot) {
+    H2_CUDA(cudaFuncSetAttribute(h2::k_rowgemm_tc<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc_smem<S, NT>()));
+    int occ = 0;
+    H2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h2::k_rowgemm_tc<S, NT>,
+                                                          h2::tc::kThreads, tc_smem<S, NT>()));
+    const int by_smem = smem_sm / (tc_smem<S, NT>() + 1024);
+    const int by_tmem = 512 / (NT < 32 ? 32 : NT);
+    h->tc_occupancy[slot] = occ;
+    h->tc_blocks[slot] = std::max(1, std::min(by_smem, by_tmem)) * nsm;
+    return H2_OK;
+}
+
+// dynamic shared memory limits and the persistent grid (resident CTAs x SMs)
+template <typename S>
+int tc_setup(h2_handle h) {
+    int nsm = 0, smem_sm = 0;
+    H2_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    H2_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+    H2_TRY((tc_setup_nt<S, 64>(h, nsm, smem_sm, 0)));
+    H2_TRY((tc_setup_nt<S, 32>(h, nsm, smem_sm, 1)));
+    H2_TRY((tc_setup_nt<S, 16>(h, nsm, smem_sm, 2)));
+    return H2_OK;
+}
+
+template <class A>
+void launch_rows_tc(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate,
+                    int nrhs, int c0, int nt, int* err, const int* blocks) {
+    if constexpr (std::is_same<A, h2::BF16>::value || std::is_same<A, h2::F32>::value) {
+        using S = typename A::S;
+        const S* o = static_cast<const S*>(ops);
+        float* v = static_cast<float*>(vec);
+        const int slot = nt == 64 ? 0 : nt == 32 ? 1 : 2;
+        const unsigned n = unsigned(std::min<int64_t>(R.n, blocks[slot]));
+        if (nt == 64)
+            h2::k_rowgemm_tc<S, 64><<<n, h2::tc::kThreads, tc_smem<S, 64>(), s>>>(
+                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col, o, v,
+                accumulate, nrhs, c0, err);
+        else if (nt == 32)
+            h2::k_rowgemm_tc<S, 32><<<n, h2::tc::kThreads, tc_smem<S, 32>(), s>>>(
+                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col, o, v,
+                accumulate, nrhs, c0, err);
+        else
+            h2::k_rowgemm_tc<S, 16><<<n, h2::tc::kThreads, tc_smem<S, 16>(), s>>>(
+                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col, o, v,
+                accumulate, nrhs, c0, err);
+    }
+}
+
+struct Tile {
+    int c0, width;
+    bool tc;
+};
+
+// RHS tiles of a block-row step: tensor-core tiles first (if on), the rest on
+// the CUDA cores, widest first
+template <class A>
+std::vector<Tile> row_tiles(h2_handle h, int nrhs) {
+    std::vector<Tile> t;
+    int c = 0;
+    if (tc_on<A>(h))
+        for (int w = 64; w >= 16; w /= 2)
+            while (nrhs - c >= w) { t.push_back({c, w, true}); c += w; }
+    for (int w = max_tile<A>(); w >= 1; w /= 2)
+        while (nrhs - c >= w) { t.push_back({c, w, false}); c += w; }
     return t;
 }
 
@@ -371,6 +477,18 @@ int upload(h2_handle h) {
     H2_TRY(dev_upload(h, &h->lr_uoff, P.lr_uoff));
     H2_TRY(dev_upload(h, &h->lr_voff, P.lr_voff));
     H2_TRY(dev_upload(h, &h->lr_toff, P.lr_toff));
+    if (tc_on<A>(h)) {
+        if constexpr (std::is_same<A, h2::BF16>::value || std::is_same<A, h2::F32>::value)
+            H2_TRY(tc_setup<typename A::S>(h));
+        void* e = nullptr;
+        H2_TRY(dev_alloc(h, &e, sizeof(int)));
+        H2_CUDA(cudaMemset(e, 0, sizeof(int)));
+        h->tc_err = static_cast<int*>(e);
+        void* ph = nullptr;
+        H2_CUDA(cudaMallocHost(&ph, sizeof(int)));
+        h->tc_err_host = static_cast<int*>(ph);
+        *h->tc_err_host = 0;
+    }
     H2_CUDA(cudaDeviceSynchronize());
     H2_TRY(autotune<A>(h));
     return H2_OK;
@@ -468,11 +586,19 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
     V* phi = vec + P.phi_base * nrhs;
     int64_t& nl = h->launches;
     const auto tiles = rhs_tiles<A>(nrhs);
+    const auto rtiles = row_tiles<A>(h, nrhs);
+    bool used_tc = false;
     auto rows = [&](const DevRowTasks& R, int accumulate) {
         if (R.n == 0) return;
-        for (const auto& tl : tiles) {
+        for (const auto& tl : rtiles) {
             ++nl;
-            launch_rows<A>(R, ops, vec, s, accumulate, nrhs, tl.first, tl.second);
+            if (tl.tc) {
+                used_tc = true;
+                launch_rows_tc<A>(R, ops, vec, s, accumulate, nrhs, tl.c0, tl.width, h->tc_err,
+                                  h->tc_blocks);
+            } else {
+                launch_rows<A>(R, ops, vec, s, accumulate, nrhs, tl.c0, tl.width);
+            }
         }
     };
 
@@ -493,7 +619,7 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
         // empty leaves keep phi = 0: clear once, the block rows overwrite the rest
         cudaMemsetAsync(phi, 0, sizeof(V) * t.N * nrhs, s);
         rows(h->leaf, 0);
-    } else if constexpr (!std::is_same<A, h2::DF>::value) {
+    } else if constexpr (!std::is_same<A, h2::DF>::value && !std::is_same<A, h2::BF16>::value) {
         using T = typename A::V;
         for (const auto& tl : tiles) {
             ++nl;
@@ -502,7 +628,7 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
         }
     }
     mark(h, s, ST_LOWRANK);
-    if constexpr (!std::is_same<A, h2::DF>::value) {
+    if constexpr (!std::is_same<A, h2::DF>::value && !std::is_same<A, h2::BF16>::value) {
         using T = typename A::V;
         if (H.variant == H2_PLUS_H_STAR && P.lr_tlen > 0) {
             T* tt = static_cast<T*>(h->lr_t);
@@ -544,8 +670,33 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
     ++nl;
     h2::k_scatter<A><<<nblocks(t.N * nrhs, 256), 256, 0, s>>>(phi, nrhs, h->perm, Y, ldy, t.N);
     mark(h, s, ST_N);
+    if (used_tc) H2_CUDA(cudaMemcpyAsync(h->tc_err_host, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaGetLastError());
     return H2_OK;
+}
+
+// the pipeline in the handle's storage
+int matvec_dispatch(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int nrhs,
+                    cudaStream_t s) {
+    switch (h->host.storage) {
+        case H2_F64: return matvec_one<h2::F64>(h, X, ldx, Y, ldy, nrhs, s);
+        case H2_F32: return matvec_one<h2::F32>(h, X, ldx, Y, ldy, nrhs, s);
+        case H2_DF64: return matvec_one<h2::DF>(h, X, ldx, Y, ldy, nrhs, s);
+        default: return matvec_one<h2::BF16>(h, X, ldx, Y, ldy, nrhs, s);
+    }
+}
+
+int upload_any(h2_handle h) {
+    switch (h->host.storage) {
+        case H2_F64: return upload<h2::F64>(h);
+        case H2_F32: return upload<h2::F32>(h);
+        case H2_DF64: return upload<h2::DF>(h);
+        default: return upload<h2::BF16>(h);
+    }
+}
+
+size_t entry_bytes(int storage) {
+    return storage == H2_F32 ? 4 : storage == H2_BF16 ? 2 : 8;
 }
 
 }  // namespace
@@ -569,8 +720,15 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     h2_build_opts o;
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    if (o.storage != H2_F64 && o.storage != H2_F32 && o.storage != H2_DF64)
+    if (o.storage != H2_F64 && o.storage != H2_F32 && o.storage != H2_DF64 && o.storage != H2_BF16)
         return fail(H2_E_INVALID_ARG, "unknown storage");
+    if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(H2_E_INVALID_ARG, "tensor_cores must be 0 or 1");
+    if (o.tensor_cores && o.storage != H2_F32)
+        return fail(H2_E_INVALID_ARG, "tensor_cores applies to H2_F32 storage (H2_BF16 always uses them)");
+    if (o.storage == H2_BF16 && o.near_mode == 1)
+        return fail(H2_E_UNSUPPORTED, "bf16 storage evaluates the near field from stored blocks only");
+    if (o.storage == H2_BF16 && variant == H2_PLUS_H_STAR)
+        return fail(H2_E_UNSUPPORTED, "(H2+H)* is built for fp64 and fp32 storage");
     if (o.near_mode < 0 || o.near_mode > 2) return fail(H2_E_INVALID_ARG, "unknown near_mode");
     if (o.storage == H2_DF64 && o.near_mode == 1)
         return fail(H2_E_UNSUPPORTED, "df64 storage evaluates the near field from stored blocks only");
@@ -604,6 +762,7 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     H.variant = variant;
     H.storage = o.storage;
     H.near_mode = o.near_mode;
+    H.tensor_cores = o.tensor_cores;
     H.eps_far = o.eps_far > 0 ? o.eps_far : tol;
     H.eps_ver = o.eps_ver > 0 ? o.eps_ver : tol;
     try {
@@ -620,9 +779,7 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
             return fail(H2_E_NO_DEVICE, "no CUDA device");
         }
         H2_CUDA(cudaGetDevice(&h->device));
-        int rc = (o.storage == H2_F64)   ? upload<h2::F64>(h.get())
-                 : (o.storage == H2_F32) ? upload<h2::F32>(h.get())
-                                         : upload<h2::DF>(h.get());
+        int rc = upload_any(h.get());
         if (rc != H2_OK) {
             h2_destroy(h.release());
             return rc;
@@ -638,13 +795,13 @@ int h2_convert(h2_handle src, int storage, h2_handle* out) {
     if (!out) return fail(H2_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!src) return fail(H2_E_INVALID_ARG, "src is NULL");
-    if (storage != H2_F64 && storage != H2_F32 && storage != H2_DF64)
+    if (storage != H2_F64 && storage != H2_F32 && storage != H2_DF64 && storage != H2_BF16)
         return fail(H2_E_INVALID_ARG, "unknown storage");
     const bool stored = src->host.packed.near_stored;
-    if (storage == H2_DF64 && !stored)
-        return fail(H2_E_UNSUPPORTED, "df64 storage needs stored near-field blocks; the source "
-                                      "evaluates them on the fly");
-    if (storage == H2_DF64 && src->host.variant == H2_PLUS_H_STAR)
+    if ((storage == H2_DF64 || storage == H2_BF16) && !stored)
+        return fail(H2_E_UNSUPPORTED, "df64 / bf16 storage needs stored near-field blocks; the "
+                                      "source evaluates them on the fly");
+    if ((storage == H2_DF64 || storage == H2_BF16) && src->host.variant == H2_PLUS_H_STAR)
         return fail(H2_E_UNSUPPORTED, "(H2+H)* is built for fp64 and fp32 storage");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -660,10 +817,9 @@ int h2_convert(h2_handle src, int storage, h2_handle* out) {
     }
     h->host.storage = storage;
     h->host.near_mode = stored ? 2 : 1;
+    if (storage != H2_F32) h->host.tensor_cores = 0;
     H2_CUDA(cudaGetDevice(&h->device));
-    int rc = (storage == H2_F64)   ? upload<h2::F64>(h.get())
-             : (storage == H2_F32) ? upload<h2::F32>(h.get())
-                                   : upload<h2::DF>(h.get());
+    int rc = upload_any(h.get());
     if (rc != H2_OK) {
         h2_destroy(h.release());
         return rc;
@@ -692,10 +848,9 @@ int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
         int rc = next_event_set(h);
         if (rc != H2_OK) return rc;
     }
-    const int st = h->host.storage;
-    return (st == H2_F64)   ? matvec_one<h2::F64>(h, X, ldx, Y, ldy, nrhs, s)
-           : (st == H2_F32) ? matvec_one<h2::F32>(h, X, ldx, Y, ldy, nrhs, s)
-                            : matvec_one<h2::DF>(h, X, ldx, Y, ldy, nrhs, s);
+    if (h->tc_err_host && *h->tc_err_host)
+        return fail(H2_E_CUDA, "a tensor-core product gave up waiting for its MMAs");
+    return matvec_dispatch(h, X, ldx, Y, ldy, nrhs, s);
 }
 
 int h2_info(h2_handle h, h2_stats* st) {
@@ -731,7 +886,7 @@ int h2_info(h2_handle h, h2_stats* st) {
         for (int l = B.lmin; l <= t.kappa; ++l) pairs += int64_t((*B.il)[l].idx.size());
         st->m2l_pairs[b] = pairs;
     }
-    const int64_t ts = H.storage == H2_F32 ? 4 : 8;
+    const int64_t ts = int64_t(entry_bytes(H.storage));
     int64_t nbasis = 0, ntrans = 0, nlr = 0;
     for (const auto& B : H.bases) {
         for (const auto& U : B.U) nbasis += int64_t(U.size());
@@ -749,6 +904,10 @@ int h2_info(h2_handle h, h2_stats* st) {
     st->near_stored = P.near_stored;
     st->rw_m2l = h->m2l.rw;
     st->rw_leaf = h->leaf.rw;
+    for (int k = 0; k < 3; ++k) {
+        st->tc_blocks[k] = h->tc_blocks[k];
+        st->tc_occupancy[k] = h->tc_occupancy[k];
+    }
     st->vlen = P.vlen;
     st->bytes_lowrank = nlr * ts;
     st->near_pairs = H.near_pairs;
@@ -832,6 +991,7 @@ void h2_destroy(h2_handle h) {
         if (h->lrt_alloc) cudaFree(h->lrt_alloc);
         for (void* p : h->gm_allocs) cudaFree(p);
         for (auto& e : h->ev_pool) cudaEventDestroy(e);
+        if (h->tc_err_host) cudaFreeHost(h->tc_err_host);
     }
     delete h;
 }
@@ -893,13 +1053,10 @@ extern "C" int h2_matvec_noalloc(h2_handle h, const double* X, double* Y, void* 
     h->lr_t = base + vec_bytes;
     h->profile = false;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int st = h->host.storage;
     const int64_t N = h->host.tree.N;
     const int saved_nrhs = h->vec_nrhs;
     h->vec_nrhs = 1;
-    int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, X, N, Y, N, 1, s)
-             : (st == H2_F32) ? matvec_one<h2::F32>(h, X, N, Y, N, 1, s)
-                              : matvec_one<h2::DF>(h, X, N, Y, N, 1, s);
+    int rc = matvec_dispatch(h, X, N, Y, N, 1, s);
     h->vec_nrhs = saved_nrhs;
     h->vec = saved_vec;
     h->lr_t = saved_lrt;
@@ -957,11 +1114,8 @@ int gm_norm(h2_handle h, const double* w, double* nrm, cudaStream_t s) {
 
 // y = shift x + scale K~ x
 int gm_apply(h2_handle h, double shift, double scale, const double* x, double* y, cudaStream_t s) {
-    const int st = h->host.storage;
     const int64_t N = h->host.tree.N;
-    int rc = (st == H2_F64)   ? matvec_one<h2::F64>(h, x, N, y, N, 1, s)
-             : (st == H2_F32) ? matvec_one<h2::F32>(h, x, N, y, N, 1, s)
-                              : matvec_one<h2::DF>(h, x, N, y, N, 1, s);
+    int rc = matvec_dispatch(h, x, N, y, N, 1, s);
     if (rc != H2_OK) return rc;
     h2::k_axpby<<<nblocks(N, 256), 256, 0, s>>>(shift, x, scale, y, N);
     return H2_OK;
@@ -1103,7 +1257,9 @@ extern "C" int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale
         // iterative refinement: residual r = b - A_res x in fp64 with h_res, correction
         // from GMRES on the faster operator of h; the inner tolerance follows the
         // inner operator's precision
-        const double floor_inner = h->host.storage == H2_F32 ? 1e-5 : 1e-10;
+        const double floor_inner = h->host.storage == H2_F32    ? 1e-5
+                                   : h->host.storage == H2_BF16 ? 1e-2
+                                                                : 1e-10;
         double* r = h->gm_r;
         double* dx = h->gm_d;
         H2_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
@@ -1322,6 +1478,7 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
     for (int i = 0; i < n; ++i) {
         if (!hs[i]) return fail(H2_E_INVALID_ARG, "NULL handle in the batch");
         if (hs[i]->host.storage != storage) return fail(H2_E_INVALID_ARG, "handles differ in storage");
+        if (storage == H2_BF16) return fail(H2_E_UNSUPPORTED, "batched products use fp64, fp32 or df64 storage");
         if (!hs[i]->host.packed.near_stored)
             return fail(H2_E_UNSUPPORTED, "batched products need the stored near field (near_mode 2)");
         if (hs[i]->host.variant == H2_PLUS_H_STAR)
@@ -1632,10 +1789,7 @@ size_t req_doubles(h2_server S, int64_t N) {
 
 int matvec_any(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k,
                cudaStream_t st) {
-    const int stor = h->host.storage;
-    return (stor == H2_F64)   ? matvec_one<h2::F64>(h, X, ldx, Y, ldy, k, st)
-           : (stor == H2_F32) ? matvec_one<h2::F32>(h, X, ldx, Y, ldy, k, st)
-                              : matvec_one<h2::DF>(h, X, ldx, Y, ldy, k, st);
+    return matvec_dispatch(h, X, ldx, Y, ldy, k, st);
 }
 
 // y = A x for every request in rs (all on geometry g, operator h): one
@@ -1923,7 +2077,8 @@ extern "C" int h2_server_create(const h2_handle* geoms, const h2_handle* res_geo
             return fail(H2_E_INVALID_ARG, "a handle is in use by another solve server");
         S->geoms.push_back(geoms[g]);
         S->res.push_back(rh);
-        S->floor.push_back(rh == geoms[g] ? 0.0 : (geoms[g]->host.storage == H2_F32 ? 1e-5 : 1e-10));
+        const int gs = geoms[g]->host.storage;
+        S->floor.push_back(rh == geoms[g] ? 0.0 : (gs == H2_F32 ? 1e-5 : gs == H2_BF16 ? 1e-2 : 1e-10));
         maxN = std::max(maxN, geoms[g]->host.tree.N);
     }
     const size_t budget = o.workspace_bytes > 0 ? size_t(o.workspace_bytes)

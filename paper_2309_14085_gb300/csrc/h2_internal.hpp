@@ -143,6 +143,7 @@ struct Host {
     int variant = 0;
     int storage = 0;
     int near_mode = 0;               // 0 default, 1 on the fly, 2 stored
+    int tensor_cores = 0;            // fp32 storage: multi-RHS tiles on tcgen05 (tf32)
     double eps_far = 0, eps_ver = 0;
     Tree tree;
     Lists lists;

@@ -3,6 +3,9 @@
 // Every kernel is templated on an arithmetic policy:
 //   F64  -- operators, coefficients and sums in IEEE double (FP64 pipe);
 //   F32  -- everything in float (FP32 pipe);
+//   BF16 -- operators stored in bfloat16 (8-bit significand), coefficients and
+//           sums in float; products with 16 or more right-hand sides run on
+//           the tensor cores (tc_kernels.cuh);
 //   DF   -- "double-float": every operator entry and coefficient is a pair
 //           (hi, lo) of floats with hi + lo equal to the fp64 value to 48
 //           significant bits, and every multiply-add runs as error-free
@@ -33,6 +36,7 @@
 //        x = the neighbours' q then the leaf's u, y = phi_X (L2P fused).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,6 +75,24 @@ struct F32 {
     __device__ static V shfl_xor(V a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
     __device__ static S lget(const L& l, int k) {
         return k == 0 ? l.x : (k == 1 ? l.y : (k == 2 ? l.z : l.w));
+    }
+};
+
+struct BF16 {
+    using S = __nv_bfloat16;
+    using V = float;
+    using L = uint2;        // four entries (rows start on 4-entry boundaries)
+    static constexpr int W = 4;
+    __device__ static V zero() { return 0.0f; }
+    __device__ static V mac(V acc, float a, V x) { return fmaf(a, x, acc); }
+    __device__ static V add(V a, V b) { return a + b; }
+    __device__ static V from_double(double a) { return float(a); }
+    __device__ static double to_double(V a) { return double(a); }
+    __device__ static V shfl_xor(V a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    // entry k of the load as float: a bfloat16 is the upper half of a float
+    __device__ static float lget(const L& l, int k) {
+        const uint32_t w = k < 2 ? l.x : l.y;
+        return __uint_as_float((k & 1) ? (w & 0xFFFF0000u) : (w << 16));
     }
 };
 

@@ -96,6 +96,27 @@ def _has_gpu():
         return False
 
 
+def test_bf16_and_tensor_core_options_are_validated():
+    P = inputs.points(300, 2, 2)
+    with pytest.raises(H2Error) as e:
+        H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, storage="bf16", near="fly", host_only=True)
+    assert e.value.code == -5
+    with pytest.raises(H2Error) as e:
+        H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, storage="bf16", variant="h2plush",
+                 host_only=True)
+    assert e.value.code == -5
+    with pytest.raises(H2Error) as e:
+        H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, tensor_cores=True, host_only=True)
+    assert e.value.code == -1                     # tf32 tensor cores are for fp32 storage
+    A = H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, storage="bf16", host_only=True)
+    B = H2Matrix(P, "log2d", leaf_size=16, tol=1e-6, storage="f32", tensor_cores=True,
+                 host_only=True)
+    a, b = A.info(), B.info()
+    assert a["near_stored"] == 1 and b["near_stored"] == 0
+    assert a["bytes_m2l"] * 4 == H2Matrix(P, "log2d", leaf_size=16, tol=1e-6,
+                                          host_only=True).info()["bytes_m2l"]
+
+
 def test_near_field_storage_accounting():
     P = inputs.points(4096, 2, 1001)
     S = H2Matrix(P, "log2d", leaf_size=64, tol=1e-6, host_only=True).info()
