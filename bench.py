@@ -224,21 +224,25 @@ def bench_ours(args, rank, world):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_ms = float(te.item())
 
-    # roofline of the dominant kernel (stage timed with CUDA events)
+    # roofline of the dominant kernel (stage timed with CUDA events) among the
+    # stages whose algorithmic bytes are known: M2L, the stored leaf rows, and
+    # the gather / scatter between user and tree order
     per = {k: v / max(calls, 1) for k, v in stages.items()}
-    dom = max(per, key=per.get)
     # coefficient bytes (fp64, float pairs, float, float); operator entry bytes
     # are already in the stored-byte counts of h2_info
     vs = {"f64": 8, "df64": 8, "f32": 4, "bf16": 4}[args.storage]
+    known = {"m2l": info["bytes_m2l"] + (info["m2l_src_coeffs"] + info["m2l_dst_coeffs"]) * vs * nrhs,
+             "gather": N * nrhs * (8 + vs) + N * 8, "scatter": N * nrhs * (vs + 8) + N * 8}
+    if info["near_stored"]:
+        known["leaf"] = info["bytes_leaf_rows"] + (info["leaf_src_coeffs"] + N) * vs * nrhs
+    dom_all = max(per, key=per.get)
+    dom = dom_all if dom_all in known or dom_all == "leaf" else "m2l"
     hbm, how = _peaks()
-    roof = {"kernel": dom, "stage_ms": {k: round(v, 4) for k, v in per.items()},
+    roof = {"kernel": dom, "dominant_stage": dom_all, "stage_ms": {k: round(v, 4) for k, v in per.items()},
             "profiled_ms_per_step": round(prof_ms_step, 4)}
-    if dom == "m2l" or (dom == "leaf" and info["near_stored"]):
+    if dom in known:
         # operators once per product, coefficients once per right-hand side
-        if dom == "m2l":
-            alg = info["bytes_m2l"] + (info["m2l_src_coeffs"] + info["m2l_dst_coeffs"]) * vs * nrhs
-        else:
-            alg = info["bytes_leaf_rows"] + (info["leaf_src_coeffs"] + N) * vs * nrhs
+        alg = known[dom]
         sec = per[dom] / 1e3
         ach = alg / sec / 1e9
         traffic = None
@@ -248,9 +252,9 @@ def bench_ours(args, rank, world):
         roof.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s",
                     frac=round(ach / hbm, 4), traffic=traffic, alg_bytes=alg,
                     peak_source=f"{how} hbm_gbs (of measured)")
-        if args.storage == "f64":
+        if args.storage == "f64" and dom == "m2l":
             # one fp64 multiply-add per stored 8-byte entry: the FP64 pipe bound
-            fma = alg / 8 / sec / 1e12
+            fma = info["bytes_m2l"] / 8 * nrhs / sec / 1e12
             roof["fp64_fma_tflops"] = round(2 * fma, 3)
             roof["fp64_frac_of_nominal_1.25"] = round(2 * fma / 1.25, 4)
     else:

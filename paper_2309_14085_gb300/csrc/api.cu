@@ -73,6 +73,7 @@ struct h2_handle_s {
     void* vec_alloc = nullptr;    // owned allocations of vec / lr_t (regrown for more RHS)
     void* lrt_alloc = nullptr;
     int64_t* perm = nullptr;
+    int64_t* iperm = nullptr;      // user index -> tree position
     int64_t* leaf_ptr = nullptr;
     int64_t* near_ptr = nullptr;
     int64_t* near_idx = nullptr;
@@ -281,12 +282,11 @@ template <class A> bool tc_on(h2_handle h) {
     else return false;
 }
 
-template <typename S, int NT> constexpr int tc_smem() {
-    return 2 * (h2::tc::kATileBytes + NT * h2::tc::kChunkBytes) + 64;
-}
+template <typename S, int NT> constexpr int tc_smem() { return h2::tc_smem_bytes<S, NT>(); }
 
-// Resident CTAs per SM from the two budgets that bind: shared memory (the
-// SM's opt-in maximum, 1 KB reserved per CTA) and TMEM (512 columns per SM).
+// Resident CTAs per SM from the budgets that bind: shared memory (the SM's
+// opt-in maximum, 1 KB reserved per CTA), TMEM (512 columns per SM) and
+// registers (64K per SM).
 template <typename S, int NT>
 int tc_setup_nt(h2_handle h, int nsm, int smem_sm, int slot) {
     H2_CUDA(cudaFuncSetAttribute(h2::k_rowgemm_tc<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -294,10 +294,13 @@ int tc_setup_nt(h2_handle h, int nsm, int smem_sm, int slot) {
     int occ = 0;
     H2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h2::k_rowgemm_tc<S, NT>,
                                                           h2::tc::kThreads, tc_smem<S, NT>()));
+    cudaFuncAttributes fa;
+    H2_CUDA(cudaFuncGetAttributes(&fa, h2::k_rowgemm_tc<S, NT>));
     const int by_smem = smem_sm / (tc_smem<S, NT>() + 1024);
     const int by_tmem = 512 / (NT < 32 ? 32 : NT);
+    const int by_regs = 65536 / (std::max(fa.numRegs, 1) * h2::tc::kThreads);
     h->tc_occupancy[slot] = occ;
-    h->tc_blocks[slot] = std::max(1, std::min(by_smem, by_tmem)) * nsm;
+    h->tc_blocks[slot] = std::max(1, std::min(std::min(by_smem, by_tmem), by_regs)) * nsm;
     return H2_OK;
 }
 
@@ -436,6 +439,11 @@ int upload(h2_handle h) {
     }
     H2_TRY(grow_vec(h, 1));
     H2_TRY(dev_upload(h, &h->perm, t.perm));
+    {
+        std::vector<int64_t> ip(t.perm.size());
+        for (size_t i = 0; i < t.perm.size(); ++i) ip[size_t(t.perm[i])] = int64_t(i);
+        H2_TRY(dev_upload(h, &h->iperm, ip));
+    }
     H2_TRY(dev_upload(h, &h->leaf_ptr, t.leaf_ptr));
     H2_TRY(dev_upload(h, &h->near_ptr, P.near_ptr));
     H2_TRY(dev_upload(h, &h->near_idx, P.near_idx));
@@ -604,7 +612,10 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
 
     mark(h, s, ST_GATHER);
     ++nl;
-    h2::k_gather<A><<<nblocks(t.N * nrhs, 256), 256, 0, s>>>(X, ldx, nrhs, h->perm, q, t.N);
+    if (nrhs == 1 || nrhs > 64)      // the transposing kernels hold up to 64 columns
+        h2::k_gather<A><<<nblocks(t.N * nrhs, 256), 256, 0, s>>>(X, ldx, nrhs, h->perm, q, t.N);
+    else
+        h2::k_gather_t<A><<<nblocks(t.N, h2::kTransRows), 256, 0, s>>>(X, ldx, nrhs, h->iperm, q, t.N);
     mark(h, s, ST_P2M);
     rows(h->p2m, 0);
     mark(h, s, ST_M2M);
@@ -668,7 +679,10 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
     }
     mark(h, s, ST_SCATTER);
     ++nl;
-    h2::k_scatter<A><<<nblocks(t.N * nrhs, 256), 256, 0, s>>>(phi, nrhs, h->perm, Y, ldy, t.N);
+    if (nrhs == 1 || nrhs > 64)
+        h2::k_scatter<A><<<nblocks(t.N * nrhs, 256), 256, 0, s>>>(phi, nrhs, h->perm, Y, ldy, t.N);
+    else
+        h2::k_scatter_t<A><<<nblocks(t.N, h2::kTransRows), 256, 0, s>>>(phi, nrhs, h->iperm, Y, ldy, t.N);
     mark(h, s, ST_N);
     if (used_tc) H2_CUDA(cudaMemcpyAsync(h->tc_err_host, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaGetLastError());

@@ -210,6 +210,50 @@ __global__ void k_scatter(const typename A::V* __restrict__ phi, int nrhs,
     Y[int64_t(c) * ldy + perm[i]] = A::to_double(phi[t]);
 }
 
+// 2 to 64 right-hand sides: a CTA takes 32 consecutive user indices j and all
+// columns, reads each column's 32 entries (coalesced), transposes through
+// shared memory and writes each point's row of nrhs coefficients at its tree
+// position iperm[j] (contiguous), or the reverse for the scatter.
+constexpr int kTransRows = 32;
+
+template <class A>
+__global__ void __launch_bounds__(256) k_gather_t(const double* __restrict__ X, int64_t ldx, int nrhs,
+                                                 const int64_t* __restrict__ iperm,
+                                                 typename A::V* __restrict__ q, int64_t N) {
+    using V = typename A::V;
+    __shared__ V tile[kTransRows][65];
+    const int64_t j0 = int64_t(blockIdx.x) * kTransRows;
+    const int n = (N - j0 < kTransRows) ? int(N - j0) : kTransRows;
+    for (int idx = threadIdx.x; idx < kTransRows * nrhs; idx += blockDim.x) {
+        const int c = idx / kTransRows, jj = idx - c * kTransRows;
+        if (jj < n) tile[jj][c] = A::from_double(X[int64_t(c) * ldx + j0 + jj]);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kTransRows * nrhs; idx += blockDim.x) {
+        const int jj = idx / nrhs, c = idx - jj * nrhs;
+        if (jj < n) q[iperm[j0 + jj] * nrhs + c] = tile[jj][c];
+    }
+}
+
+template <class A>
+__global__ void __launch_bounds__(256) k_scatter_t(const typename A::V* __restrict__ phi, int nrhs,
+                                                  const int64_t* __restrict__ iperm,
+                                                  double* __restrict__ Y, int64_t ldy, int64_t N) {
+    using V = typename A::V;
+    __shared__ V tile[kTransRows][65];
+    const int64_t j0 = int64_t(blockIdx.x) * kTransRows;
+    const int n = (N - j0 < kTransRows) ? int(N - j0) : kTransRows;
+    for (int idx = threadIdx.x; idx < kTransRows * nrhs; idx += blockDim.x) {
+        const int jj = idx / nrhs, c = idx - jj * nrhs;
+        if (jj < n) tile[jj][c] = phi[iperm[j0 + jj] * nrhs + c];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kTransRows * nrhs; idx += blockDim.x) {
+        const int c = idx / kTransRows, jj = idx - c * kTransRows;
+        if (jj < n) Y[int64_t(c) * ldy + j0 + jj] = A::to_double(tile[jj][c]);
+    }
+}
+
 // ---- block-row GEMV: M2L, L2L and the stored near field (+ fused L2P) ---------
 // One CTA (8 warps) per task.  The gathered coefficients of an NR-column tile
 // (columns c0 .. c0 + NR - 1 of nrhs) are staged through a 32 KB shared-memory

@@ -6,7 +6,7 @@
 // 5th-generation tensor cores instead of re-streaming the operators per
 // CUDA-core tile.
 //
-// Per CTA (128 threads = 4 warps; persistent: tasks blockIdx.x, + gridDim.x, ...):
+// Per CTA (256 threads = 8 warps; persistent: tasks blockIdx.x, + gridDim.x, ...):
 //   * warp 0 allocates NT columns of tensor memory (TMEM) for the 128 x NT fp32
 //     accumulator once, and the chunk mbarriers are initialised once;
 //   * the K dimension runs in chunks of 128 bytes per row (64 bf16 or 32 fp32
@@ -20,8 +20,11 @@
 //   * thread 0 issues four tcgen05.mma per chunk (K = 32 bytes each) and
 //     commits them to the chunk's mbarrier; two chunk buffers alternate, so
 //     staging of chunk g + 1 overlaps the MMAs of chunk g;
-//   * each warp reads its 32 accumulator rows back with tcgen05.ld and adds
-//     them to Y (fp32).
+//   * warp w reads accumulator rows 32 (w mod 4) .. + 31, columns of half
+//     w / 4, back with tcgen05.ld and adds them to Y (fp32).
+// Staging maps a warp onto 8 rows (or RHS columns) x 4 words of one 16-byte
+// core-matrix slot, so its shared-memory stores hit all 32 banks once; each
+// thread issues all its global loads of a chunk before its stores.
 // Every mbarrier wait is bounded: on expiry the CTA records an error code in
 // *err, waits (bounded) for its MMAs in flight, frees its TMEM and returns.
 #pragma once
@@ -33,7 +36,7 @@
 namespace h2 {
 namespace tc {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;           // 8 warps
 constexpr int kRowsTile = 128;              // MMA M
 constexpr int kChunkBytes = 128;            // K bytes per row per chunk
 constexpr int kATileBytes = kRowsTile * kChunkBytes;
@@ -123,20 +126,18 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  ::"r"(smem_u32(bar)) : "memory");
 }
 
-// 32 lanes x 32 bits, 16 consecutive columns: thread t of the warp receives
-// row (lane base + t), columns col .. col + 15
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 32 lanes x 32 bits, 8 consecutive columns: thread t of the warp receives
+// row (lane base + t), columns col .. col + 7
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[7])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
 
 // byte offset of (row r, K byte kb) in a staged tile (no-swizzle K-major)
@@ -149,21 +150,32 @@ template <> struct In<__nv_bfloat16> {
     using T = __nv_bfloat16;                 // MMA input element
     static constexpr bool BF = true;
     static constexpr uint32_t FMT = 1;
-    __device__ static T cvt(float x) { return __float2bfloat16_rn(x); }
+    static constexpr int KPW = 2;            // K entries per 32-bit word
+    // two consecutive K entries of one column -> one word (lower K in the low half)
+    __device__ static uint32_t pack(const float (&x)[2]) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(x[0], x[1]);
+        return *reinterpret_cast<const uint32_t*>(&b);
+    }
 };
 template <> struct In<float> {
     using T = float;                         // tf32: fp32 container, tf32 multiply
     static constexpr bool BF = false;
     static constexpr uint32_t FMT = 2;
-    __device__ static T cvt(float x) { return x; }
+    static constexpr int KPW = 1;
+    __device__ static uint32_t pack(const float (&x)[1]) { return __float_as_uint(x[0]); }
 };
 
 }  // namespace tc
 
 // Block-row GEMM on tensor cores; S = stored operator type (bf16 or fp32),
-// coefficients are fp32.  Dynamic shared memory: 2 x (16 KB + NT * 128 B) + 64.
+// coefficients are fp32.  Dynamic shared memory: tc_smem_bytes<S, NT>().
 template <typename S, int NT>
-__global__ void __launch_bounds__(tc::kThreads) k_rowgemm_tc(
+__host__ __device__ constexpr int tc_smem_bytes() {
+    return 2 * (tc::kATileBytes + NT * tc::kChunkBytes + (tc::kChunkBytes / int(sizeof(S))) * 8) + 64;
+}
+
+template <typename S, int NT>
+__global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
     int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
     const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
     const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
@@ -171,16 +183,20 @@ __global__ void __launch_bounds__(tc::kThreads) k_rowgemm_tc(
     const S* __restrict__ ops, float* __restrict__ vec, int accumulate, int nrhs, int c0,
     int* __restrict__ err) {
     using In = tc::In<S>;
-    using T = typename In::T;
     static_assert(NT == 16 || NT == 32 || NT == 64, "RHS tile");
-    constexpr int ES = int(sizeof(T));
+    constexpr int ES = int(sizeof(S));
     constexpr int KC = tc::kChunkBytes / ES;            // K entries per chunk
+    constexpr int KPW = In::KPW;
     constexpr int kBTileBytes = NT * tc::kChunkBytes;
-    constexpr int kBufBytes = tc::kATileBytes + kBTileBytes;
+    constexpr int kBufBytes = tc::kATileBytes + kBTileBytes + KC * 8;
     constexpr uint32_t kCols = NT < 32 ? 32 : NT;       // TMEM columns (power of 2, >= 32)
     constexpr uint32_t kIdesc = tc::instr_desc(In::FMT, tc::kRowsTile, NT);
+    constexpr int kAUnits = tc::kRowsTile * 16;         // 8-byte units of a full A tile
+    constexpr int kAPer = kAUnits / tc::kThreads;       // per thread
+    constexpr int kBItems = KC * NT / KPW;              // 32-bit words of a B tile
+    constexpr int kBPer = kBItems / tc::kThreads;
+    static_assert(kBItems % tc::kThreads == 0 && kAUnits % tc::kThreads == 0, "staging split");
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* buf[2] = {smem, smem + kBufBytes};
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kBufBytes + 16);
     int* fail = reinterpret_cast<int*>(smem + 2 * kBufBytes + 20);
@@ -202,96 +218,117 @@ __global__ void __launch_bounds__(tc::kThreads) k_rowgemm_tc(
     bool ok = true;
 
     for (int64_t t = blockIdx.x; t < ntask && ok; t += gridDim.x) {
-    const int kp = kpad[t];
-    const int nr = rows[t];
-    const int64_t e0 = seg_ptr[t], e1 = seg_ptr[t + 1];
-    const int ktot = (e1 > e0) ? seg_col[e1 - 1] + seg_len[e1 - 1] : 0;
-    const S* Am = ops + aoff[t];
-    float* y = vec + dst[t] * nrhs + c0;
-    const int ncols = min(NT, nrhs - c0);
-    const int nchunk = (kp + KC - 1) / KC;
-    if (nchunk == 0) {                                   // no columns: y = 0 (or unchanged)
-        for (int j = tid; j < nr * ncols && !accumulate; j += tc::kThreads)
-            y[int64_t(j / ncols) * nrhs + (j % ncols)] = 0.0f;
-    }
-    for (int m0 = 0; m0 < nr && ok && nchunk > 0; m0 += tc::kRowsTile) {
-        const int mt = min(tc::kRowsTile, nr - m0);     // rows of this tile
-        int64_t ef = e0;
-        for (int ch = 0; ch < nchunk; ++ch, ++g) {
-            const int b = int(g & 1);
-            if (g >= 2) {                               // MMAs of chunk g - 2 read this buffer
-                if (tid == 0 && !tc::mbar_wait(&bar[b], ((g - 2) >> 1) & 1, tc::kWaitLimit)) *fail = 1;
+        const int kp = kpad[t];
+        const int nr = rows[t];
+        const int64_t e0 = seg_ptr[t], e1 = seg_ptr[t + 1];
+        const S* Am = ops + aoff[t];
+        float* y = vec + dst[t] * nrhs + c0;
+        const int ncols = min(NT, nrhs - c0);
+        const int nchunk = (kp + KC - 1) / KC;
+        if (nchunk == 0) {                               // no columns: y = 0 (or unchanged)
+            for (int j = tid; j < nr * ncols && !accumulate; j += tc::kThreads)
+                y[int64_t(j / ncols) * nrhs + (j % ncols)] = 0.0f;
+        }
+        for (int m0 = 0; m0 < nr && ok && nchunk > 0; m0 += tc::kRowsTile) {
+            const int mt = min(tc::kRowsTile, nr - m0);  // rows of this tile
+            for (int ch = 0; ch < nchunk; ++ch, ++g) {
+                const int b = int(g & 1);
+                uint8_t* At = smem + b * kBufBytes;
+                uint8_t* Bt = At + tc::kATileBytes;
+                int64_t* src = reinterpret_cast<int64_t*>(Bt + kBTileBytes);
+                const int k0 = ch * KC;
+                // source coefficient of every K entry of the chunk (-1: zero)
+                if (tid < KC) {
+                    const int k = k0 + tid;
+                    int64_t si = -1;
+                    for (int64_t e = e0; e < e1; ++e) {
+                        const int sc = seg_col[e];
+                        if (k < sc) break;
+                        if (k < sc + seg_len[e]) { si = seg_off[e] + (k - sc); break; }
+                    }
+                    src[tid] = si;
+                }
+                if (g >= 2) {                            // MMAs of chunk g - 2 read this buffer
+                    if (tid == 0 && !tc::mbar_wait(&bar[b], ((g - 2) >> 1) & 1, tc::kWaitLimit)) *fail = 1;
+                }
                 __syncthreads();
                 if (*fail) { ok = false; break; }
-            }
-            uint8_t* At = buf[b];
-            uint8_t* Bt = buf[b] + tc::kATileBytes;
-            const int k0 = ch * KC;
-            // A: the tile's rows x 128 bytes, 8-byte units, consecutive threads along a row
-            for (int u = tid; u < mt * 16; u += tc::kThreads) {
-                const int r = u >> 4, q = u & 15;
-                const int kk = k0 + q * (8 / int(sizeof(S)));
-                uint2 v = make_uint2(0u, 0u);
-                if (kk < kp) v = __ldg(reinterpret_cast<const uint2*>(Am + int64_t(m0 + r) * kp + kk));
-                *reinterpret_cast<uint2*>(At + tc::tile_off(r, q * 8)) = v;
-            }
-            // X: KC entries x NT columns from the task's segments (columns fastest)
-            const int cw = min(KC, kp - k0);
-            while (ef < e1 && seg_col[ef] + seg_len[ef] <= k0) ++ef;
-            for (int64_t e = ef; e < e1; ++e) {
-                const int sc = seg_col[e];
-                if (sc >= k0 + cw) break;
-                const int lo = max(sc, k0), hi = min(sc + seg_len[e], k0 + cw);
-                const float* src = vec + (seg_off[e] + (lo - sc)) * nrhs + c0;
-                const int n = (hi - lo) * NT;
-                for (int j = tid; j < n; j += tc::kThreads) {
-                    const int jj = j / NT, c = j - jj * NT;
-                    const float x = c < ncols ? src[int64_t(jj) * nrhs + c] : 0.0f;
-                    *reinterpret_cast<T*>(Bt + tc::tile_off(c, (lo - k0 + jj) * ES)) = In::cvt(x);
+                // A: 8 rows x 4 units of one slot per warp; loads first, then stores
+                uint2 av[kAPer];
+#pragma unroll
+                for (int i = 0; i < kAPer; ++i) {
+                    const int u = tid + i * tc::kThreads;
+                    const int r = (u >> 7) * 8 + (u & 7), q = (u >> 3) & 15;
+                    const int kk = k0 + q * (8 / ES);
+                    av[i] = make_uint2(0u, 0u);
+                    if (r < mt && kk < kp)
+                        av[i] = __ldg(reinterpret_cast<const uint2*>(Am + int64_t(m0 + r) * kp + kk));
+                }
+                // X: column c_lo = lane & 7 of a group of 8, word w = (lane >> 3) & 3 of the slot
+                float bv[kBPer][KPW];
+#pragma unroll
+                for (int i = 0; i < kBPer; ++i) {
+                    const int v = tid + i * tc::kThreads;
+                    const int c = ((v >> 5) % (NT / 8)) * 8 + (v & 7);
+                    const int kb = ((v >> 5) / (NT / 8)) * (4 * KPW) + ((v >> 3) & 3) * KPW;
+#pragma unroll
+                    for (int j = 0; j < KPW; ++j) {
+                        const int64_t si = src[kb + j];
+                        bv[i][j] = (si >= 0 && c < ncols) ? vec[si * nrhs + c0 + c] : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < kAPer; ++i) {
+                    const int u = tid + i * tc::kThreads;
+                    const int r = (u >> 7) * 8 + (u & 7), q = (u >> 3) & 15;
+                    if (r < mt) *reinterpret_cast<uint2*>(At + tc::tile_off(r, q * 8)) = av[i];
+                }
+#pragma unroll
+                for (int i = 0; i < kBPer; ++i) {
+                    const int v = tid + i * tc::kThreads;
+                    const int c = ((v >> 5) % (NT / 8)) * 8 + (v & 7);
+                    const int kb = ((v >> 5) / (NT / 8)) * (4 * KPW) + ((v >> 3) & 3) * KPW;
+                    *reinterpret_cast<uint32_t*>(Bt + tc::tile_off(c, kb * ES)) = In::pack(bv[i]);
+                }
+                tc::fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(At), b0 = tc::smem_u32(Bt);
+#pragma unroll
+                    for (int s = 0; s < tc::kChunkBytes / 32; ++s) {   // K = 32 bytes per MMA
+                        const uint64_t ad = tc::smem_desc(a0 + s * 256, 128, 1024);
+                        const uint64_t bd = tc::smem_desc(b0 + s * 256, 128, 1024);
+                        tc::mma<In::BF>(tmem, ad, bd, kIdesc, (ch > 0 || s > 0) ? 1u : 0u);
+                    }
+                    tc::mma_commit(&bar[b]);
                 }
             }
-            for (int j = max(ktot - k0, 0) * NT + tid; j < KC * NT; j += tc::kThreads) {
-                const int jj = j / NT, c = j - jj * NT;
-                *reinterpret_cast<T*>(Bt + tc::tile_off(c, jj * ES)) = In::cvt(0.0f);
-            }
-            tc::fence_async_smem();
+            if (!ok) break;
+            // all MMAs of this row tile complete (the last commit covers earlier ones)
+            if (tid == 0 && g > 0 && !tc::mbar_wait(&bar[(g - 1) & 1], ((g - 1) >> 1) & 1, tc::kWaitLimit))
+                *fail = 1;
             __syncthreads();
-            if (tid == 0) {
-                tc::tc_fence_after();
-                const uint32_t a0 = tc::smem_u32(At), b0 = tc::smem_u32(Bt);
+            if (*fail) { ok = false; break; }
+            tc::tc_fence_after();
+            const int quarter = warp & 3, half = warp >> 2;
+            const int row = m0 + quarter * 32 + lane;
+            const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16);
 #pragma unroll
-                for (int s = 0; s < tc::kChunkBytes / 32; ++s) {   // K = 32 bytes per MMA
-                    const uint64_t ad = tc::smem_desc(a0 + s * 256, 128, 1024);
-                    const uint64_t bd = tc::smem_desc(b0 + s * 256, 128, 1024);
-                    tc::mma<In::BF>(tmem, ad, bd, kIdesc, (ch > 0 || s > 0) ? 1u : 0u);
+            for (int c8 = half * (NT / 2); c8 < (half + 1) * (NT / 2); c8 += 8) {
+                float v[8];
+                tc::tmem_ld8(tbase + uint32_t(c8), v);
+                if (row < nr) {
+                    float* yo = y + int64_t(row) * nrhs + c8;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (c8 + k < ncols) yo[k] = accumulate ? yo[k] + v[k] : v[k];
                 }
-                tc::mma_commit(&bar[b]);
             }
+            tc::tc_fence_before();
+            __syncthreads();                             // TMEM reads done before the next tile
+            tc::tc_fence_after();
         }
-        if (!ok) break;
-        // all MMAs of this row tile complete (the last commit covers earlier ones)
-        if (tid == 0 && g > 0 && !tc::mbar_wait(&bar[(g - 1) & 1], ((g - 1) >> 1) & 1, tc::kWaitLimit))
-            *fail = 1;
-        __syncthreads();
-        if (*fail) { ok = false; break; }
-        tc::tc_fence_after();
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t tbase = tmem + (uint32_t(warp * 32) << 16);
-#pragma unroll
-        for (int c16 = 0; c16 < NT; c16 += 16) {
-            float v[16];
-            tc::tmem_ld16(tbase + uint32_t(c16), v);
-            if (row < nr) {
-                float* yo = y + int64_t(row) * nrhs + c16;
-#pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    if (c16 + k < ncols) yo[k] = accumulate ? yo[k] + v[k] : v[k];
-            }
-        }
-        tc::tc_fence_before();
-        __syncthreads();                                 // TMEM reads done before the next tile
-        tc::tc_fence_after();
-    }
     }
     if (!ok) {
         // bounded wait for the MMAs still in flight before the TMEM is released

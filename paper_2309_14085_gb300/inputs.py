@@ -26,6 +26,9 @@ WORKLOADS = {
     # 2D log r, N = 2^20, kappa 7, 64 right-hand sides
     "c3_2d_log_n1048576": dict(number=3, N=1 << 20, d=2, kernel="log2d", n_max=64, eps=1e-10,
                                 nrhs=64),
+    # the same kernel, tolerance and RHS count at N = 2^16 (kappa 5): the profiling case
+    "c3s_2d_log_n65536": dict(number=3, N=1 << 16, d=2, kernel="log2d", n_max=64, eps=1e-10,
+                               nrhs=64),
 }
 
 
