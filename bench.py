@@ -343,10 +343,13 @@ def bench_batched(args):
     ncpu = os.cpu_count() or 8
 
     def build(i):
-        # large instances get more host threads
+        # large instances get more host threads; each instance goes to the device
+        # at once and drops its host operators (the batch copies device to device)
         th = max(1, min(ncpu, int(ncpu * i["N"] / 65536.0) or 1))
-        return H2Matrix(i["points"], i["kernel"], leaf_size=64, tol=1e-8, storage=args.storage,
-                        near="stored", host_only=True, threads=th)
+        m = H2Matrix(i["points"], i["kernel"], leaf_size=64, tol=1e-8, storage=args.storage,
+                     near="stored", threads=th)
+        m.release_host()
+        return m
 
     order = sorted(range(len(inst)), key=lambda k: -inst[k]["N"])
     mats = [None] * len(inst)
@@ -524,6 +527,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2_3d_invr_n262144")
     ap.add_argument("--storage", default="f64", choices=["f64", "df64", "f32", "bf16"])
+    ap.add_argument("--multi-rhs", default="bf16,tf32",
+                    help="default workload only: also time the 64-RHS workload on the tensor "
+                         "cores in these modes (comma list of bf16, tf32; '' for none)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="fp32 storage: RHS tiles of 16-64 columns on tcgen05 (tf32)")
     ap.add_argument("--variant", default="h2star", choices=list(VARIANT_NAMES))
@@ -606,6 +612,28 @@ def main():
         out["other_storage"] = extra
     if args.gmres_solves > 0:
         out["gmres"] = bench_gmres(getattr(args, "_handles", {}), w, nsolve=args.gmres_solves)
+    if args.multi_rhs and args.workload == "c2_3d_invr_n262144":
+        # the 64-RHS workload on the tensor cores (bf16 storage; tf32 for fp32)
+        mr = {"workload": "c3_2d_log_n1048576", "nrhs": 64}
+        for mode in [m for m in args.multi_rhs.split(",") if m]:
+            a3 = argparse.Namespace(**vars(args))
+            a3.workload, a3.nrhs, a3.steps = "c3_2d_log_n1048576", 0, 20
+            a3.storage, a3.tensor_cores = ("bf16", False) if mode == "bf16" else ("f32", True)
+            a3._handles = {}
+            try:
+                o3, _ = bench_ours(a3, rank, world)
+                r3 = o3["roofline"]
+                mr[mode] = {"value": o3["value"], "unit": UNIT, "ms_per_step": o3["ms_per_step"],
+                            "e2e": o3["e2e"]["value"], "dominant": r3["kernel"],
+                            "frac": r3.get("frac"), "achieved_gbs": r3.get("achieved"),
+                            "stage_ms": r3["stage_ms"], "clocks": o3["clocks"],
+                            "gpu_launches": o3["gpu_launches"],
+                            "tc_persistent_ctas": o3["config"]["tc_persistent_ctas"],
+                            "build_seconds": o3["config"]["build_seconds"]}
+            except Exception as e:              # report, do not lose the main line
+                mr[mode] = {"error": str(e)[:300]}
+            a3._handles = {}
+        out["multi_rhs_tensor_cores"] = mr
     if rank == 0:
         cb = run_oracle_rows(args.workload, args.cpu_seconds)
         out["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],

@@ -115,6 +115,15 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size,
              double tol, int variant, const h2_build_opts* opts, h2_handle* out);
 
 /*
+ * h2_release_host -- free the host copy of the packed operators of a handle
+ * that is on the device (the largest host allocation: every stored operator
+ * entry in fp64).  Products, solves, servers and batches keep working from the
+ * device copy; h2_convert from this handle then returns H2_E_UNSUPPORTED.
+ * Errors: H2_E_INVALID_ARG (NULL, host-only or served handle).
+ */
+int h2_release_host(h2_handle h);
+
+/*
  * h2_convert -- a second device copy of the same compressed operator in another
  * storage precision, without repeating the construction: the tree, lists,
  * pivots and packed operators of `src` are copied on the host and uploaded in

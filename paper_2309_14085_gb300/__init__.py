@@ -24,7 +24,7 @@ VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2}
 STORAGE = {"f64": 0, "f32": 1, "df64": 2, "bf16": 3}
 NEAR = {None: 0, "fly": 1, "stored": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
-EXPORTED = ("h2_build", "h2_convert", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
+EXPORTED = ("h2_build", "h2_convert", "h2_release_host", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
             "h2_batch_matvec", "h2_batch_info", "h2_batch_destroy", "h2_server_create",
             "h2_server_submit", "h2_server_wait", "h2_server_stats_get", "h2_server_destroy")
@@ -126,6 +126,7 @@ def lib():
         L.h2_batch_destroy.argtypes = [c_vp]
         L.h2_batch_destroy.restype = None
         L.h2_convert.argtypes = [c_vp, c_int, ctypes.POINTER(c_vp)]
+        L.h2_release_host.argtypes = [c_vp]
         L.h2_server_create.argtypes = [c_vp, c_vp, c_int, ctypes.POINTER(ServerOpts),
                                        ctypes.POINTER(c_vp)]
         L.h2_server_submit.argtypes = [c_vp, c_int, c_dbl, c_dbl, c_vp, c_dbl, c_int,
@@ -196,6 +197,10 @@ class H2Matrix:
         m.N, m.d, m.kernel, m.variant, m.storage = self.N, self.d, self.kernel, self.variant, storage
         m._h = h
         return m
+
+    def release_host(self):
+        """Free the host copy of the operators (the device copy stays)."""
+        _check(lib().h2_release_host(self._h))
 
     # -- the product ---------------------------------------------------------
     def matvec(self, X, out=None, stream=None):

@@ -65,7 +65,8 @@ struct h2_handle_s {
     size_t vsize = 8;             // sizeof coefficient type
     int64_t bytes_device = 0;
     // device buffers
-    void* ops = nullptr;          // stored entries (double / float / float2)
+    void* ops = nullptr;          // stored entries (double / float / float2 / bf16)
+    int64_t ops_len = 0;          // entries of ops (the host copy may have been released)
     void* xs = nullptr;           // coordinates, d x N (on-the-fly near field)
     void* vec = nullptr;          // [ q | v | u | phi ] x vec_nrhs (point-major, RHS fastest)
     void* lr_t = nullptr;         // (H2+H)* scratch V^T q_Y, x vec_nrhs
@@ -427,6 +428,7 @@ int upload(h2_handle h) {
             }
         }
         h->ops = p;
+        h->ops_len = int64_t(P.ops.size());
     }
     if (!P.near_stored) {
         using T = typename std::conditional<std::is_same<A, h2::F32>::value, float, double>::type;
@@ -804,11 +806,22 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     return H2_OK;
 }
 
+int h2_release_host(h2_handle h) {
+    g_err.clear();
+    if (!h) return fail(H2_E_INVALID_ARG, "handle is NULL");
+    if (!h->on_device) return fail(H2_E_INVALID_ARG, "a host-only handle keeps its operators");
+    if (h->server) return fail(H2_E_INVALID_ARG, "handle is in use by a solve server");
+    std::vector<double>().swap(h->host.packed.ops);
+    return H2_OK;
+}
+
 int h2_convert(h2_handle src, int storage, h2_handle* out) {
     g_err.clear();
     if (!out) return fail(H2_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!src) return fail(H2_E_INVALID_ARG, "src is NULL");
+    if (src->host.packed.ops.empty() && src->on_device && src->ops_len > 0)
+        return fail(H2_E_UNSUPPORTED, "the source's host operators were released (h2_release_host)");
     if (storage != H2_F64 && storage != H2_F32 && storage != H2_DF64 && storage != H2_BF16)
         return fail(H2_E_INVALID_ARG, "unknown storage");
     const bool stored = src->host.packed.near_stored;
@@ -1511,7 +1524,8 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
     int64_t ol = 0;
     for (int i = 0; i < n; ++i) {
         abase[i] = ol;
-        ol += (int64_t(hs[i]->host.packed.ops.size()) + 3) / 4 * 4;
+        const int64_t len = hs[i]->on_device ? hs[i]->ops_len : int64_t(hs[i]->host.packed.ops.size());
+        ol += (len + 3) / 4 * 4;
     }
     B->ops_len = ol;
     // virtual instances and the coefficient layout [Q | V | U | PHI]
@@ -1571,6 +1585,12 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
         B->ops = p;
         const size_t chunk = size_t(1) << 24;
         for (int i = 0; i < n; ++i) {
+            if (hs[i]->on_device) {
+                // the instance's operators are on this device already, in this storage
+                H2_CUDA(cudaMemcpy(static_cast<unsigned char*>(p) + size_t(abase[i]) * B->ssize, hs[i]->ops,
+                                   size_t(hs[i]->ops_len) * B->ssize, cudaMemcpyDeviceToDevice));
+                continue;
+            }
             const std::vector<double>& src = hs[i]->host.packed.ops;
             for (size_t o = 0; o < src.size(); o += chunk) {
                 const size_t c = std::min(chunk, src.size() - o);

@@ -44,3 +44,28 @@ def test_batch_equals_individual_products(storage):
                     for k, s in enumerate(specs)])[1].cpu().numpy()
     bar = 1e-4 if storage == "f32" else 1e-10
     assert np.abs(got - ref).max() <= bar * np.abs(ref).max()
+
+
+def test_batch_from_host_only_and_released_handles():
+    """A batch takes each instance's operators from the device copy when the
+    handle is on the device (its host copy may be released) and from the host
+    copy of a host-only handle; both give the instance's own product."""
+    specs = [(2, 3000, 1), (3, 4000, 2)]
+    pts = [inputs.points(N, d, 3100 + k, lo=0.0, hi=1.0) for k, (d, N, r) in enumerate(specs)]
+    kinds = ["log2d", "invr"]
+    host = H2Matrix(pts[0], kinds[0], leaf_size=64, tol=1e-8, storage="f32", near="stored",
+                    host_only=True)
+    dev = H2Matrix(pts[1], kinds[1], leaf_size=64, tol=1e-8, storage="f32", near="stored")
+    dev.release_host()
+    with pytest.raises(Exception):
+        dev.convert("f64")                     # the host operators are gone
+    B = H2Batch([host, dev], [1, 2])
+    xs = [torch.tensor(inputs.rhs(N, r, 4100 + k).reshape(N, r), device="cuda:0")
+          for k, (d, N, r) in enumerate(specs)]
+    ys = B.matvec(xs)
+    torch.cuda.synchronize()
+    for k, (d, N, r) in enumerate(specs):
+        ref_m = H2Matrix(pts[k], kinds[k], leaf_size=64, tol=1e-8, storage="f32", near="stored")
+        ref = ref_m.matvec(xs[k]).reshape(ys[k].shape).cpu().numpy()
+        got = ys[k].cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
