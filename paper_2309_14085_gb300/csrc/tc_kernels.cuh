@@ -18,8 +18,9 @@
 //     along K (leading byte offset) and 1024 B apart along M / N (stride byte
 //     offset);
 //   * thread 0 issues four tcgen05.mma per chunk (K = 32 bytes each) and
-//     commits them to the chunk's mbarrier; two chunk buffers alternate, so
-//     staging of chunk g + 1 overlaps the MMAs of chunk g;
+//     commits them to the chunk's mbarrier; two chunk buffers alternate, and
+//     each thread issues the global loads of chunk g + 1 (into registers) right
+//     after storing chunk g, so they fly during the barrier and the MMAs;
 //   * warp w reads accumulator rows 32 (w mod 4) .. + 31, columns of half
 //     w / 4, back with tcgen05.ld and adds them to Y (fp32).
 // Staging maps a warp onto 8 rows (or RHS columns) x 4 words of one 16-byte
@@ -171,7 +172,7 @@ template <> struct In<float> {
 // coefficients are fp32.  Dynamic shared memory: tc_smem_bytes<S, NT>().
 template <typename S, int NT>
 __host__ __device__ constexpr int tc_smem_bytes() {
-    return 2 * (tc::kATileBytes + NT * tc::kChunkBytes + (tc::kChunkBytes / int(sizeof(S))) * 8) + 64;
+    return 2 * (tc::kATileBytes + NT * tc::kChunkBytes) + 2 * (tc::kChunkBytes / int(sizeof(S))) * 8 + 64;
 }
 
 template <typename S, int NT>
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
     constexpr int KC = tc::kChunkBytes / ES;            // K entries per chunk
     constexpr int KPW = In::KPW;
     constexpr int kBTileBytes = NT * tc::kChunkBytes;
-    constexpr int kBufBytes = tc::kATileBytes + kBTileBytes + KC * 8;
+    constexpr int kBufBytes = tc::kATileBytes + kBTileBytes;
     constexpr uint32_t kCols = NT < 32 ? 32 : NT;       // TMEM columns (power of 2, >= 32)
     constexpr uint32_t kIdesc = tc::instr_desc(In::FMT, tc::kRowsTile, NT);
     constexpr int kAUnits = tc::kRowsTile * 16;         // 8-byte units of a full A tile
@@ -197,9 +198,10 @@ __global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
     constexpr int kBPer = kBItems / tc::kThreads;
     static_assert(kBItems % tc::kThreads == 0 && kAUnits % tc::kThreads == 0, "staging split");
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kBufBytes + 16);
-    int* fail = reinterpret_cast<int*>(smem + 2 * kBufBytes + 20);
+    int64_t* tab = reinterpret_cast<int64_t*>(smem + 2 * kBufBytes);   // [2][KC] sources
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes + 2 * KC * 8);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+    int* fail = reinterpret_cast<int*>(tmem_slot + 1);
 
     if (int64_t(blockIdx.x) >= ntask) return;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -216,6 +218,8 @@ __global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
     const uint32_t tmem = *tmem_slot;
     uint32_t g = 0;                                      // chunks issued by this CTA
     bool ok = true;
+    uint2 av[kAPer];                                     // staged loads of the next chunk
+    float bv[kBPer][KPW];
 
     for (int64_t t = blockIdx.x; t < ntask && ok; t += gridDim.x) {
         const int kp = kpad[t];
@@ -229,54 +233,61 @@ __global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
             for (int j = tid; j < nr * ncols && !accumulate; j += tc::kThreads)
                 y[int64_t(j / ncols) * nrhs + (j % ncols)] = 0.0f;
         }
+        // source coefficient of every K entry of chunk ch (-1: zero), into table slot
+        auto build_table = [&](int ch, int slot) {
+            if (tid < KC) {
+                const int k = ch * KC + tid;
+                int64_t si = -1;
+                for (int64_t e = e0; e < e1; ++e) {
+                    const int sc = seg_col[e];
+                    if (k < sc) break;
+                    if (k < sc + seg_len[e]) { si = seg_off[e] + (k - sc); break; }
+                }
+                tab[slot * KC + tid] = si;
+            }
+        };
+        // global loads of chunk ch into registers (A: 8 rows x 4 units per warp;
+        // X: column c_lo = lane & 7 of a group of 8, word (lane >> 3) & 3 of the slot)
+        auto load_chunk = [&](int m0, int mt, int ch, int slot) {
+            const int k0 = ch * KC;
+#pragma unroll
+            for (int i = 0; i < kAPer; ++i) {
+                const int u = tid + i * tc::kThreads;
+                const int r = (u >> 7) * 8 + (u & 7), q = (u >> 3) & 15;
+                const int kk = k0 + q * (8 / ES);
+                av[i] = make_uint2(0u, 0u);
+                if (r < mt && kk < kp)
+                    av[i] = __ldg(reinterpret_cast<const uint2*>(Am + int64_t(m0 + r) * kp + kk));
+            }
+            const int64_t* src = tab + slot * KC;
+#pragma unroll
+            for (int i = 0; i < kBPer; ++i) {
+                const int v = tid + i * tc::kThreads;
+                const int c = ((v >> 5) % (NT / 8)) * 8 + (v & 7);
+                const int kb = ((v >> 5) / (NT / 8)) * (4 * KPW) + ((v >> 3) & 3) * KPW;
+#pragma unroll
+                for (int j = 0; j < KPW; ++j) {
+                    const int64_t si = src[kb + j];
+                    bv[i][j] = (si >= 0 && c < ncols) ? vec[si * nrhs + c0 + c] : 0.0f;
+                }
+            }
+        };
         for (int m0 = 0; m0 < nr && ok && nchunk > 0; m0 += tc::kRowsTile) {
             const int mt = min(tc::kRowsTile, nr - m0);  // rows of this tile
+            // prologue: chunk 0's table and loads
+            build_table(0, int(g & 1));
+            __syncthreads();
+            load_chunk(m0, mt, 0, int(g & 1));
             for (int ch = 0; ch < nchunk; ++ch, ++g) {
                 const int b = int(g & 1);
                 uint8_t* At = smem + b * kBufBytes;
                 uint8_t* Bt = At + tc::kATileBytes;
-                int64_t* src = reinterpret_cast<int64_t*>(Bt + kBTileBytes);
-                const int k0 = ch * KC;
-                // source coefficient of every K entry of the chunk (-1: zero)
-                if (tid < KC) {
-                    const int k = k0 + tid;
-                    int64_t si = -1;
-                    for (int64_t e = e0; e < e1; ++e) {
-                        const int sc = seg_col[e];
-                        if (k < sc) break;
-                        if (k < sc + seg_len[e]) { si = seg_off[e] + (k - sc); break; }
-                    }
-                    src[tid] = si;
-                }
+                if (ch + 1 < nchunk) build_table(ch + 1, b ^ 1);
                 if (g >= 2) {                            // MMAs of chunk g - 2 read this buffer
                     if (tid == 0 && !tc::mbar_wait(&bar[b], ((g - 2) >> 1) & 1, tc::kWaitLimit)) *fail = 1;
                 }
                 __syncthreads();
                 if (*fail) { ok = false; break; }
-                // A: 8 rows x 4 units of one slot per warp; loads first, then stores
-                uint2 av[kAPer];
-#pragma unroll
-                for (int i = 0; i < kAPer; ++i) {
-                    const int u = tid + i * tc::kThreads;
-                    const int r = (u >> 7) * 8 + (u & 7), q = (u >> 3) & 15;
-                    const int kk = k0 + q * (8 / ES);
-                    av[i] = make_uint2(0u, 0u);
-                    if (r < mt && kk < kp)
-                        av[i] = __ldg(reinterpret_cast<const uint2*>(Am + int64_t(m0 + r) * kp + kk));
-                }
-                // X: column c_lo = lane & 7 of a group of 8, word w = (lane >> 3) & 3 of the slot
-                float bv[kBPer][KPW];
-#pragma unroll
-                for (int i = 0; i < kBPer; ++i) {
-                    const int v = tid + i * tc::kThreads;
-                    const int c = ((v >> 5) % (NT / 8)) * 8 + (v & 7);
-                    const int kb = ((v >> 5) / (NT / 8)) * (4 * KPW) + ((v >> 3) & 3) * KPW;
-#pragma unroll
-                    for (int j = 0; j < KPW; ++j) {
-                        const int64_t si = src[kb + j];
-                        bv[i][j] = (si >= 0 && c < ncols) ? vec[si * nrhs + c0 + c] : 0.0f;
-                    }
-                }
 #pragma unroll
                 for (int i = 0; i < kAPer; ++i) {
                     const int u = tid + i * tc::kThreads;
@@ -290,6 +301,8 @@ __global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
                     const int kb = ((v >> 5) / (NT / 8)) * (4 * KPW) + ((v >> 3) & 3) * KPW;
                     *reinterpret_cast<uint32_t*>(Bt + tc::tile_off(c, kb * ES)) = In::pack(bv[i]);
                 }
+                // the next chunk's loads fly during the barrier and the MMA issue
+                if (ch + 1 < nchunk) load_chunk(m0, mt, ch + 1, b ^ 1);
                 tc::fence_async_smem();
                 __syncthreads();
                 if (tid == 0) {
