@@ -312,11 +312,14 @@ typedef struct {
 /*
  * h2_batch_create -- merge n handles (any mix of N, d, kernel and depth; one
  * storage; stored near field, h2_build_opts.near_mode = 2; H2*(b+t) or
- * H2_sqrt(d)(b)) into one device layout for batched products.  Handles may be
- * host-only: their host representation is uploaded once more, into one operator
+ * H2_sqrt(d)(b)) into one device layout for batched products.  Operators are
+ * copied from the device copy of handles on the device (their host copy may be
+ * released) and from the host copy of host-only handles, into one operator
  * array.  nrhs[i] in [1, 64] (NULL = all 1) is instance i's column count.
- * Every (instance, column) pair becomes a virtual instance with its own
- * coefficients; the tasks of all of them are merged so one product is ~2 kappa_max
+ * Every (instance, tile of up to 4 columns in fp32 / 2 in fp64 and df64) pair
+ * becomes a virtual instance with its own coefficients (the tile's operators
+ * are streamed once for all its columns); the tasks of all of them are merged
+ * so one product is ~2 kappa_max
  * + 4 launches (P2M, M2M bottom-up and L2L top-down in level-synchronous steps,
  * one M2L launch, one leaf launch, gather and scatter), captured once into a
  * CUDA graph.  The handles may be destroyed afterwards.

@@ -1353,15 +1353,19 @@ extern "C" int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale
 }
 
 // ---------------------------------------------------------------------------
-// Batched products over many independent trees: every (instance, RHS column)
-// is a virtual instance with its own coefficient regions; the task lists of
+// Batched products over many independent trees: every (instance, tile of nt
+// RHS columns; nt = 4 in fp32, 2 in fp64 / double-float) is a virtual instance
+// with its own coefficient regions (point-major, nt columns per point, zero
+// columns past the instance's last); the task lists of
 // all of them are merged so that each MVP stage is one launch (M2M bottom-up
 // and L2L top-down in level-synchronous steps), and the whole sequence is
 // captured once into a CUDA graph and replayed.
 namespace {
 
-__global__ void k_batch_gather(int nv, const int64_t* __restrict__ pref, const int64_t* __restrict__ qb,
-                               const int64_t* __restrict__ pb, const int64_t* __restrict__ perm,
+// one thread per (virtual instance, point): the tile's nt columns (zero beyond ncol[v])
+__global__ void k_batch_gather(int nv, int nt, const int64_t* __restrict__ pref,
+                               const int64_t* __restrict__ qb, const int64_t* __restrict__ pb,
+                               const int32_t* __restrict__ ncol, const int64_t* __restrict__ perm,
                                const double* const* __restrict__ X, void* __restrict__ vec, int storage) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= pref[nv]) return;
@@ -1370,15 +1374,19 @@ __global__ void k_batch_gather(int nv, const int64_t* __restrict__ pref, const i
         const int mid = (lo + hi) / 2;
         if (pref[mid] <= t) lo = mid; else hi = mid;
     }
-    const int64_t i = t - pref[lo];
-    const double x = X[lo][perm[pb[lo] + i]];
-    if (storage == H2_F64) static_cast<double*>(vec)[qb[lo] + i] = x;
-    else if (storage == H2_F32) static_cast<float*>(vec)[qb[lo] + i] = float(x);
-    else static_cast<float2*>(vec)[qb[lo] + i] = h2::DF::from_double(x);
+    const int64_t i = t - pref[lo], n = pref[lo + 1] - pref[lo];
+    const int64_t src = perm[pb[lo] + i], o = (qb[lo] + i) * nt;
+    for (int c = 0; c < nt; ++c) {
+        const double x = c < ncol[lo] ? X[lo][int64_t(c) * n + src] : 0.0;
+        if (storage == H2_F64) static_cast<double*>(vec)[o + c] = x;
+        else if (storage == H2_F32) static_cast<float*>(vec)[o + c] = float(x);
+        else static_cast<float2*>(vec)[o + c] = h2::DF::from_double(x);
+    }
 }
 
-__global__ void k_batch_scatter(int nv, const int64_t* __restrict__ pref, const int64_t* __restrict__ fb,
-                                const int64_t* __restrict__ pb, const int64_t* __restrict__ perm,
+__global__ void k_batch_scatter(int nv, int nt, const int64_t* __restrict__ pref,
+                                const int64_t* __restrict__ fb, const int64_t* __restrict__ pb,
+                                const int32_t* __restrict__ ncol, const int64_t* __restrict__ perm,
                                 double* const* __restrict__ Y, const void* __restrict__ vec, int storage) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= pref[nv]) return;
@@ -1387,12 +1395,15 @@ __global__ void k_batch_scatter(int nv, const int64_t* __restrict__ pref, const 
         const int mid = (lo + hi) / 2;
         if (pref[mid] <= t) lo = mid; else hi = mid;
     }
-    const int64_t i = t - pref[lo];
-    double y;
-    if (storage == H2_F64) y = static_cast<const double*>(vec)[fb[lo] + i];
-    else if (storage == H2_F32) y = double(static_cast<const float*>(vec)[fb[lo] + i]);
-    else y = h2::DF::to_double(static_cast<const float2*>(vec)[fb[lo] + i]);
-    Y[lo][perm[pb[lo] + i]] = y;
+    const int64_t i = t - pref[lo], n = pref[lo + 1] - pref[lo];
+    const int64_t dst = perm[pb[lo] + i], o = (fb[lo] + i) * nt;
+    for (int c = 0; c < ncol[lo]; ++c) {
+        double y;
+        if (storage == H2_F64) y = static_cast<const double*>(vec)[o + c];
+        else if (storage == H2_F32) y = double(static_cast<const float*>(vec)[o + c]);
+        else y = h2::DF::to_double(static_cast<const float2*>(vec)[o + c]);
+        Y[lo][int64_t(c) * n + dst] = y;
+    }
 }
 
 }  // namespace
@@ -1400,7 +1411,10 @@ __global__ void k_batch_scatter(int nv, const int64_t* __restrict__ pref, const 
 struct h2_batch_s {
     int storage = 0, ninst = 0, nvirt = 0, device = -1;
     size_t ssize = 8, vsize = 8;
-    std::vector<int> inst_of, col_of;          // per virtual instance
+    int nt = 1;                                // RHS columns per virtual instance
+    int64_t pts_rhs = 0;                       // sum over instances of N_i nrhs_i
+    std::vector<int> inst_of, col_of, ncol;    // per virtual instance
+    int32_t* ncol_dev = nullptr;
     std::vector<int64_t> npts;                 // per virtual instance
     int64_t total_pts = 0, veclen = 0, ops_len = 0;
     void* ops = nullptr;
@@ -1474,24 +1488,25 @@ int batch_launch_all(h2_batch b, cudaStream_t s) {
     b->launches = 0;
     const int threads = 256;
     ++b->launches;
+    const int nt = b->nt;
     k_batch_gather<<<nblocks(b->total_pts, threads), threads, 0, s>>>(
-        b->nvirt, b->pref, b->qb, b->pb, b->perm, b->Xtab, b->vec, b->storage);
+        b->nvirt, nt, b->pref, b->qb, b->pb, b->ncol_dev, b->perm, b->Xtab, b->vec, b->storage);
     auto rows = [&](const DevRowTasks& R, int acc) {
         if (R.n == 0) return;
         ++b->launches;
-        launch_rows<A>(R, b->ops, b->vec, s, acc);
+        launch_rows<A>(R, b->ops, b->vec, s, acc, nt, 0, nt);
     };
     rows(b->p2m, 0);
     for (const auto& R : b->m2m) rows(R, 0);
     V* vec = static_cast<V*>(b->vec);
-    if (b->u_len > 0) cudaMemsetAsync(vec + b->u_begin, 0, sizeof(V) * b->u_len, s);
+    if (b->u_len > 0) cudaMemsetAsync(vec + b->u_begin * nt, 0, sizeof(V) * b->u_len * nt, s);
     rows(b->m2l, 0);
     for (const auto& R : b->l2l) rows(R, 1);
-    if (b->phi_len > 0) cudaMemsetAsync(vec + b->phi_begin, 0, sizeof(V) * b->phi_len, s);
+    if (b->phi_len > 0) cudaMemsetAsync(vec + b->phi_begin * nt, 0, sizeof(V) * b->phi_len * nt, s);
     rows(b->leaf, 0);
     ++b->launches;
     k_batch_scatter<<<nblocks(b->total_pts, threads), threads, 0, s>>>(
-        b->nvirt, b->pref, b->fb, b->pb, b->perm, b->Ytab, b->vec, b->storage);
+        b->nvirt, nt, b->pref, b->fb, b->pb, b->ncol_dev, b->perm, b->Ytab, b->vec, b->storage);
     return H2_OK;
 }
 
@@ -1532,12 +1547,16 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
     int64_t totN = 0, totV = 0;
     std::vector<int64_t> qoff, voff, pbase(n);
     int64_t pb = 0;
+    B->nt = storage == H2_F32 ? 4 : 2;
     for (int i = 0; i < n; ++i) {
         pbase[i] = pb;
         pb += hs[i]->host.tree.N;
-        for (int c = 0; c < (nrhs ? nrhs[i] : 1); ++c) {
+        const int r = nrhs ? nrhs[i] : 1;
+        B->pts_rhs += hs[i]->host.tree.N * r;
+        for (int c = 0; c < r; c += B->nt) {
             B->inst_of.push_back(i);
             B->col_of.push_back(c);
+            B->ncol.push_back(std::min(B->nt, r - c));
             B->npts.push_back(hs[i]->host.tree.N);
             qoff.push_back(totN);
             voff.push_back(totV);
@@ -1610,10 +1629,10 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
                 }
             }
         }
-        e = cudaMalloc(&p, std::max<size_t>(size_t(B->veclen), 1) * B->vsize);
+        e = cudaMalloc(&p, std::max<size_t>(size_t(B->veclen) * B->nt, 1) * B->vsize);
         if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         B->allocs.push_back(p);
-        B->bytes_device += int64_t(B->veclen) * int64_t(B->vsize);
+        B->bytes_device += int64_t(B->veclen) * B->nt * int64_t(B->vsize);
         B->vec = p;
     }
     std::vector<int64_t> perm;
@@ -1630,6 +1649,10 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
     H2_TRY(bupload(B.get(), &B->qb, qbv));
     H2_TRY(bupload(B.get(), &B->fb, fbv));
     H2_TRY(bupload(B.get(), &B->pb, pbv));
+    {
+        std::vector<int32_t> nc(B->ncol.begin(), B->ncol.end());
+        H2_TRY(bupload(B.get(), &B->ncol_dev, nc));
+    }
     std::vector<const double*> nullx(B->nvirt, nullptr);
     std::vector<double*> nully(B->nvirt, nullptr);
     H2_TRY(bupload(B.get(), &B->Xtab, nullx));
@@ -1695,7 +1718,7 @@ extern "C" int h2_batch_info(h2_batch b, h2_batch_stats* st) {
     std::memset(st, 0, sizeof(*st));
     st->instances = b->ninst;
     st->virtual_instances = b->nvirt;
-    st->points_times_rhs = b->total_pts;
+    st->points_times_rhs = b->pts_rhs;
     st->launches_per_product = b->launches;
     st->m2m_steps = int(b->m2m.size());
     st->l2l_steps = int(b->l2l.size());

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("storage", ["f32", "f64", "df64"])
 def test_batch_equals_individual_products(storage):
     rng = np.random.default_rng(3000)
-    specs = [(2, 1200, 1), (3, 5000, 2), (2, 9000, 3), (3, 900, 1), (2, 20000, 2), (3, 12000, 1)]
+    specs = [(2, 1200, 1), (3, 5000, 2), (2, 9000, 7), (3, 900, 1), (2, 20000, 5), (3, 12000, 3)]
     mats, xs, nr = [], [], []
     for k, (d, N, r) in enumerate(specs):
         P = inputs.points(N, d, 3000 + k, lo=0.0, hi=1.0)
@@ -24,7 +24,9 @@ def test_batch_equals_individual_products(storage):
         nr.append(r)
     B = H2Batch(mats, nr)
     info = B.info()
-    assert info["instances"] == 6 and info["virtual_instances"] == sum(nr)
+    nt = 4 if storage == "f32" else 2                # RHS columns per virtual instance
+    assert info["instances"] == 6 and info["virtual_instances"] == sum(-(-r // nt) for r in nr)
+    assert info["points_times_rhs"] == sum(s[1] * s[2] for s in specs)
     kmax = max(m.info()["kappa"] for m in mats)
     assert info["launches_per_product"] <= 2 * kmax + 4
     for rep in range(2):                      # the graph replays with fresh inputs
