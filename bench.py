@@ -133,6 +133,25 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ----------------------------------------------------------------------------- replicas
+def replica_max_ms(ms_local, world, device):
+    """The slowest rank's time: every rank runs an independent replica of the
+    same work (no collective on the data path), so the job takes the maximum."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ms_total_local, units_per_step, steps, world, device):
+    """(ms per step of the slowest rank, whole-job units per second): the units
+    of all ranks over the slowest rank's time."""
+    ms_step = replica_max_ms(ms_total_local, world, device) / steps
+    return ms_step, world * units_per_step / (ms_step / 1e3)
+
+
 # ----------------------------------------------------------------------------- our arm
 def bench_ours(args, rank, world):
     import torch
@@ -180,13 +199,7 @@ def bench_ours(args, rank, world):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    value = world * N * nrhs / (ms_step / 1e3)
+    ms_step, value = replica_throughput(e0.elapsed_time(e1), N * nrhs, args.steps, world, dev)
 
     # the same steps again with CUDA events between the pipeline stages (on the
     # stream the kernels run on): per-stage durations and the launch count
@@ -218,11 +231,7 @@ def bench_ours(args, rank, world):
         hy.copy_(dy, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e_steps
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_ms = float(te.item())
+    e2e_ms = replica_max_ms(e0.elapsed_time(e1) / e_steps, world, dev)
 
     # roofline of the dominant kernel (stage timed with CUDA events) among the
     # stages whose algorithmic bytes are known: M2L, the stored leaf rows, and
