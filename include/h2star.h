@@ -87,6 +87,10 @@ typedef struct {
     int    tensor_cores;   /* H2_F32 only: 1 = RHS tiles of 16-64 columns run on the
                               tensor cores in tf32 (10-bit significand multiplies,
                               fp32 accumulate); 0 (default) = fp32 CUDA-core FMA     */
+    int    m2l_mode;       /* H2_F32 only: 1 = the coupling blocks T_{X,Y} = G(t^{X,i},
+                              t^{Y,i}) (§3.6.4) are evaluated in each product from the
+                              pivot coordinates instead of being stored; 0 (default) =
+                              stored blocks                                          */
 } h2_build_opts;
 
 typedef struct h2_handle_s* h2_handle;
@@ -187,6 +191,8 @@ typedef struct {
     int     tc_blocks[3];          /* tensor-core products: persistent CTAs per launch for
                                       RHS tiles of 64 / 32 / 16 (0: no tensor cores)     */
     int     tc_occupancy[3];       /* the runtime's resident-CTA estimate per SM (report) */
+    int     m2l_fly;               /* 1: M2L evaluated from pivot coordinates           */
+    int64_t m2l_entries;           /* entries of all T_{X,Y} (sum of rows x columns)     */
 } h2_stats;
 
 /* h2_info -- fill *st (host).  Errors: H2_E_INVALID_ARG. */

@@ -36,7 +36,8 @@ class BuildOpts(ctypes.Structure):
                 ("use_domain", ctypes.c_int), ("domain_lo", ctypes.c_double * 3),
                 ("domain_side", ctypes.c_double), ("threads", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("kparam", ctypes.c_double),
-                ("near_mode", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("near_mode", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("m2l_mode", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +56,8 @@ class Stats(ctypes.Structure):
                 ("bytes_lowrank", ctypes.c_int64),
                 ("bytes_device", ctypes.c_int64), ("alg_bytes_per_rhs", ctypes.c_int64),
                 ("build_seconds", ctypes.c_double), ("tc_blocks", ctypes.c_int * 3),
-                ("tc_occupancy", ctypes.c_int * 3)]
+                ("tc_occupancy", ctypes.c_int * 3), ("m2l_fly", ctypes.c_int),
+                ("m2l_entries", ctypes.c_int64)]
 
 
 class GmresStats(ctypes.Structure):
@@ -161,7 +163,7 @@ class H2Matrix:
 
     def __init__(self, points, kernel, leaf_size=64, tol=1e-8, variant="h2star", storage="f64",
                  eps_far=None, eps_ver=None, kappa=None, domain=None, threads=0,
-                 host_only=False, kparam=None, near=None, tensor_cores=False):
+                 host_only=False, kparam=None, near=None, tensor_cores=False, m2l=None):
         P = np.ascontiguousarray(points, dtype=np.float64)
         if P.ndim != 2:
             raise ValueError("points must be N x d")
@@ -183,6 +185,7 @@ class H2Matrix:
         o.kparam = kparam or 0.0
         o.near_mode = NEAR[near]
         o.tensor_cores = int(tensor_cores)
+        o.m2l_mode = {None: 0, "stored": 0, "fly": 1}[m2l]
         h = ctypes.c_void_p()
         _check(lib().h2_build(P.ctypes.data, self.N, self.d, KERNELS[kernel], leaf_size, tol,
                               VARIANTS[variant], ctypes.byref(o), ctypes.byref(h)))

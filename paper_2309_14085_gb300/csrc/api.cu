@@ -68,6 +68,7 @@ struct h2_handle_s {
     void* ops = nullptr;          // stored entries (double / float / float2 / bf16)
     int64_t ops_len = 0;          // entries of ops (the host copy may have been released)
     void* xs = nullptr;           // coordinates, d x N (on-the-fly near field)
+    void* px = nullptr;           // pivot coordinates, d x vlen (on-the-fly M2L)
     void* vec = nullptr;          // [ q | v | u | phi ] x vec_nrhs (point-major, RHS fastest)
     void* lr_t = nullptr;         // (H2+H)* scratch V^T q_Y, x vec_nrhs
     int vec_nrhs = 0;             // right-hand sides the buffers hold
@@ -372,7 +373,7 @@ int autotune(h2_handle h) {
     const int rws[3] = {2, 4, 8};
     for (int li = 0; li < 2; ++li) {
         DevRowTasks& R = *lists[li];
-        if (R.n == 0) continue;
+        if (R.n == 0 || (li == 0 && h->host.m2l_fly)) continue;   // no stored M2L blocks
         double t[3];
         for (int k = 0; k < 3; ++k) {
             R.rw = rws[k];
@@ -438,6 +439,14 @@ int upload(h2_handle h) {
         T* p = nullptr;
         H2_TRY(dev_upload(h, &p, xs));
         h->xs = p;
+    }
+    if (H.m2l_fly) {
+        if constexpr (std::is_same<A, h2::F32>::value) {
+            std::vector<float> pxf(P.pivot_x.begin(), P.pivot_x.end());
+            float* p = nullptr;
+            H2_TRY(dev_upload(h, &p, pxf));
+            h->px = p;
+        }
     }
     H2_TRY(grow_vec(h, 1));
     H2_TRY(dev_upload(h, &h->perm, t.perm));
@@ -541,6 +550,40 @@ void launch_leaf_d(h2_handle h, cudaStream_t s, int nrhs, int c0, int nr) {
     }
 }
 
+// M2L from the pivot coordinates (fp32)
+template <int D, int KIND, int NR>
+void launch_m2l(h2_handle h, cudaStream_t s, int nrhs, int c0) {
+    const h2::Host& H = h->host;
+    const h2::Packed& P = H.packed;
+    const DevRowTasks& R = h->m2l;
+    if (R.n == 0) return;
+    h2::k_m2l_fly<float, D, KIND, NR><<<unsigned(R.n), 256, 0, s>>>(
+        R.n, R.dst, R.rows, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
+        static_cast<const float*>(h->px), P.vlen, P.v_base, P.u_base, static_cast<float*>(h->vec),
+        float(1.0 / (H.kern.param * H.kern.param)), float(H.kern.diag()), nrhs, c0);
+}
+
+template <int D, int KIND>
+void launch_m2l_nr(h2_handle h, cudaStream_t s, int nrhs, int c0, int nr) {
+    switch (nr) {
+        case 16: launch_m2l<D, KIND, 16>(h, s, nrhs, c0); break;
+        case 8: launch_m2l<D, KIND, 8>(h, s, nrhs, c0); break;
+        case 4: launch_m2l<D, KIND, 4>(h, s, nrhs, c0); break;
+        case 2: launch_m2l<D, KIND, 2>(h, s, nrhs, c0); break;
+        default: launch_m2l<D, KIND, 1>(h, s, nrhs, c0); break;
+    }
+}
+
+template <int D>
+void launch_m2l_d(h2_handle h, cudaStream_t s, int nrhs, int c0, int nr) {
+    switch (h->host.kern.kind) {
+        case 0: launch_m2l_nr<D, 0>(h, s, nrhs, c0, nr); break;
+        case 1: launch_m2l_nr<D, 1>(h, s, nrhs, c0, nr); break;
+        case 2: launch_m2l_nr<D, 2>(h, s, nrhs, c0, nr); break;
+        default: launch_m2l_nr<D, 3>(h, s, nrhs, c0, nr); break;
+    }
+}
+
 void mark(h2_handle h, cudaStream_t s, int stage) {
     if (h->profile) cudaEventRecord(h->ev[stage], s);
 }
@@ -624,7 +667,17 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
     for (int l = K - 1; l >= 1; --l) rows(h->m2m[l], 0);
     mark(h, s, ST_M2L);
     if (P.vlen > 0) cudaMemsetAsync(u, 0, sizeof(V) * P.vlen * nrhs, s);
-    rows(h->m2l, 0);
+    if (H.m2l_fly) {
+        if constexpr (std::is_same<A, h2::F32>::value) {
+            for (const auto& tl : tiles) {
+                ++nl;
+                if (d == 2) launch_m2l_d<2>(h, s, nrhs, tl.first, tl.second);
+                else launch_m2l_d<3>(h, s, nrhs, tl.first, tl.second);
+            }
+        }
+    } else {
+        rows(h->m2l, 0);
+    }
     mark(h, s, ST_L2L);
     for (int l = 2; l <= K; ++l) rows(h->l2l[l], 1);
     mark(h, s, ST_LEAF);
@@ -741,6 +794,9 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(H2_E_INVALID_ARG, "tensor_cores must be 0 or 1");
     if (o.tensor_cores && o.storage != H2_F32)
         return fail(H2_E_INVALID_ARG, "tensor_cores applies to H2_F32 storage (H2_BF16 always uses them)");
+    if (o.m2l_mode < 0 || o.m2l_mode > 1) return fail(H2_E_INVALID_ARG, "unknown m2l_mode");
+    if (o.m2l_mode == 1 && o.storage != H2_F32)
+        return fail(H2_E_UNSUPPORTED, "M2L on the fly is built for fp32 storage");
     if (o.storage == H2_BF16 && o.near_mode == 1)
         return fail(H2_E_UNSUPPORTED, "bf16 storage evaluates the near field from stored blocks only");
     if (o.storage == H2_BF16 && variant == H2_PLUS_H_STAR)
@@ -779,6 +835,7 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     H.storage = o.storage;
     H.near_mode = o.near_mode;
     H.tensor_cores = o.tensor_cores;
+    H.m2l_fly = o.m2l_mode;
     H.eps_far = o.eps_far > 0 ? o.eps_far : tol;
     H.eps_ver = o.eps_ver > 0 ? o.eps_ver : tol;
     try {
@@ -825,6 +882,8 @@ int h2_convert(h2_handle src, int storage, h2_handle* out) {
     if (storage != H2_F64 && storage != H2_F32 && storage != H2_DF64 && storage != H2_BF16)
         return fail(H2_E_INVALID_ARG, "unknown storage");
     const bool stored = src->host.packed.near_stored;
+    if (src->host.m2l_fly && storage != H2_F32)
+        return fail(H2_E_UNSUPPORTED, "the source evaluates M2L on the fly (fp32 only)");
     if ((storage == H2_DF64 || storage == H2_BF16) && !stored)
         return fail(H2_E_UNSUPPORTED, "df64 / bf16 storage needs stored near-field blocks; the "
                                       "source evaluates them on the fly");
@@ -934,6 +993,13 @@ int h2_info(h2_handle h, h2_stats* st) {
     for (int k = 0; k < 3; ++k) {
         st->tc_blocks[k] = h->tc_blocks[k];
         st->tc_occupancy[k] = h->tc_occupancy[k];
+    }
+    st->m2l_fly = H.m2l_fly;
+    st->m2l_entries = 0;
+    for (int64_t k = 0; k < P.m2l.size(); ++k) {
+        int64_t cols = 0;
+        for (int64_t e = P.m2l.seg_ptr[k]; e < P.m2l.seg_ptr[k + 1]; ++e) cols += P.m2l.seg_len[e];
+        st->m2l_entries += int64_t(P.m2l.rows[k]) * cols;
     }
     st->vlen = P.vlen;
     st->bytes_lowrank = nlr * ts;
@@ -1521,6 +1587,7 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
         if (!hs[i]) return fail(H2_E_INVALID_ARG, "NULL handle in the batch");
         if (hs[i]->host.storage != storage) return fail(H2_E_INVALID_ARG, "handles differ in storage");
         if (storage == H2_BF16) return fail(H2_E_UNSUPPORTED, "batched products use fp64, fp32 or df64 storage");
+        if (hs[i]->host.m2l_fly) return fail(H2_E_UNSUPPORTED, "batched products use stored M2L blocks");
         if (!hs[i]->host.packed.near_stored)
             return fail(H2_E_UNSUPPORTED, "batched products need the stored near field (near_mode 2)");
         if (hs[i]->host.variant == H2_PLUS_H_STAR)

@@ -503,7 +503,9 @@ std::string operators(const Host& H, Basis& B) {
                     const int64_t Xc = X * (int64_t(1) << d) + c;
                     solve_rows(B.tau[l + 1][Xc], B.Ut[l + 1][Xc]);
                 }
-            // M2L: concatenated T_{X,Y} over Y in the list, r_X x sum r_Y
+            // M2L: concatenated T_{X,Y} over Y in the list, r_X x sum r_Y (not
+            // stored when the product evaluates it from the pivots)
+            if (H.m2l_fly) continue;
             const Csr& L = (*B.il)[l];
             int64_t kx = 0;
             for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) kx += B.rank(l, L.idx[e]);
@@ -725,14 +727,37 @@ void pack(Host& H) {
                 for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) kx += B.rank(l, L.idx[e]);
                 if (r == 0 || kx == 0) continue;
                 const int64_t kp = pad4(kx);
-                const int64_t o = place(int64_t(r) * kp);
-                P.m2l.add(P.u_base + P.voff[slot(b, l, X)], r, int32_t(kp), o);
-                copies.push_back({&B.T[l][X], o, r, kx, kp});
+                if (H.m2l_fly) {
+                    P.m2l.add(P.u_base + P.voff[slot(b, l, X)], r, int32_t(kp), 0);
+                } else {
+                    const int64_t o = place(int64_t(r) * kp);
+                    P.m2l.add(P.u_base + P.voff[slot(b, l, X)], r, int32_t(kp), o);
+                    copies.push_back({&B.T[l][X], o, r, kx, kp});
+                }
                 for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
                     const int64_t sy = slot(b, l, L.idx[e]);
                     if (P.rank[sy] > 0) P.m2l.seg(P.v_base + P.voff[sy], P.rank[sy]);
                 }
                 P.m2l.close();
+            }
+        }
+    }
+    if (H.m2l_fly) {
+        P.m2l.entries = 0;                              // nothing stored
+        // pivot coordinates in the coefficient layout: slot (b, l, X) holds the
+        // incoming pivots t^{X,i} of that cluster, in pivot order
+        P.pivot_x.assign(size_t(d) * size_t(P.vlen), 0.0);
+        for (int b = 0; b < P.nb; ++b) {
+            const Basis& B = H.bases[b];
+            for (int l = 0; l <= K; ++l) {
+                if (l < B.lmin) continue;
+                for (int64_t X = 0; X < t.nboxes(l); ++X) {
+                    const auto& tau = B.tau[l][X];
+                    const int64_t o = P.voff[slot(b, l, X)];
+                    for (size_t a = 0; a < tau.size(); ++a)
+                        for (int k = 0; k < d; ++k)
+                            P.pivot_x[size_t(k) * P.vlen + o + a] = t.x[size_t(tau[a]) * d + k];
+                }
             }
         }
     }

@@ -113,6 +113,8 @@ struct RowTasks {
 // is [ q (N) | v (vlen) | u (vlen) | phi (N) ].
 struct Packed {
     int nb = 0;                       // nested bases (1 or 2)
+    std::vector<double> pivot_x;      // M2L on the fly: d x vlen pivot coordinates, in the
+                                      // v / u coefficient layout (coordinate-major)
     int near_stored = 0;              // 1: near field stored as leaf block rows
     int64_t box_total = 0;            // boxes over levels 0..kappa
     std::vector<int64_t> box_base;    // first box id of each level
@@ -144,6 +146,7 @@ struct Host {
     int storage = 0;
     int near_mode = 0;               // 0 default, 1 on the fly, 2 stored
     int tensor_cores = 0;            // fp32 storage: multi-RHS tiles on tcgen05 (tf32)
+    int m2l_fly = 0;                 // 1: M2L from pivot coordinates, T not stored
     double eps_far = 0, eps_ver = 0;
     Tree tree;
     Lists lists;

@@ -543,6 +543,143 @@ __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t lea
     }
 }
 
+// ---- M2L evaluated on the fly (fp32) ----------------------------------------
+// In H2* the coupling block T_{X,Y} is the kernel matrix between the incoming
+// pivots of X and those of Y (§3.6.4), so u_X = sum_{Y in IL(X)} G(t^{X,i},
+// t^{Y,i}) v_Y can be evaluated from pivot coordinates instead of streaming
+// the stored blocks: px holds the coordinate k of the pivot whose v / u
+// coefficient sits at offset o of the v (or u) region at px[k * vlen + o].
+// log r uses the accurate logf (the nested bases amplify entry errors);
+// param2 = 1 / c^2 for the IMQ.
+template <int KIND>
+__device__ __forceinline__ float m2l_kernel(float r2, float param2, float diag) {
+    if (r2 == 0.0f) return diag;
+    if constexpr (KIND == 0) return 0.5f * logf(r2);
+    else if constexpr (KIND == 1) return rsqrtf(r2);
+    else if constexpr (KIND == 2) return rsqrtf(fmaf(r2, param2, 1.0f));
+    else return __expf(-sqrtf(r2));
+}
+
+// One CTA per target (the M2L task list); the sources -- the task's segments,
+// concatenated -- are staged in tiles of 256 as float4 (coordinates, then the
+// coefficient for one RHS; coordinates only for NR > 1, coefficients apart),
+// so a pair costs one shared load; each thread evaluates four sources at a
+// time into four partial sums; the 256 threads cover the target rows in 64- or
+// 128-row groups, the groups taking alternate sets of four sources (4 or 2
+// parts), and the parts' sums are added at the end.
+template <typename T, int D, int KIND, int NR>
+__global__ void __launch_bounds__(256) k_m2l_fly(
+    int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
+    const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
+    const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
+    const T* __restrict__ px, int64_t vlen, int64_t v_base, int64_t u_base,
+    T* __restrict__ vec, T param2, T diag, int nrhs, int c0) {
+    static_assert(D <= 3, "float4 staging holds up to 3 coordinates");
+    constexpr int TILE = 256;
+    constexpr bool PACKED = NR == 1;                  // (x, y, z, v); 2D: (x, y, v, -)
+    constexpr int VSLOT = D == 3 ? 3 : 2;
+    __shared__ float4 s4[TILE];
+    __shared__ T sv[PACKED || NR == 1 ? 1 : TILE * NR];
+    __shared__ T red[3 * 64 * NR];
+    const int64_t t = blockIdx.x;
+    if (t >= ntask) return;
+    // stale entries past a partial tile stay finite: zero the tiles once
+    for (int j = threadIdx.x; j < TILE; j += blockDim.x) {
+        s4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (NR > 1) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) sv[j * NR + c] = T(0);
+        }
+    }
+    const int nr = rows[t];
+    const int64_t e0 = seg_ptr[t], e1 = seg_ptr[t + 1];
+    const int ktot = (e1 > e0) ? seg_col[e1 - 1] + seg_len[e1 - 1] : 0;
+    const int64_t d0 = dst[t] - u_base;                 // pivot index of the first target row
+    const int R = nr <= 64 ? 64 : 128;                   // rows per group
+    const int nparts = int(blockDim.x) / R;              // 4 or 2
+    const int part = int(threadIdx.x) / R;
+    const int step = 4 * nparts;
+    const int li = int(threadIdx.x) % R;
+    for (int i0 = 0; i0 < nr; i0 += R) {
+        const int i = i0 + li;
+        const bool active = i < nr;
+        float xi[3] = {0.f, 0.f, 0.f};
+        T acc[4][NR];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc[q][c] = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) xi[k] = active ? px[k * vlen + d0 + i] : T(0);
+        int64_t ef = e0;
+        for (int ch = 0; ch < ktot; ch += TILE) {
+            const int cw = min(TILE, ktot - ch);
+            __syncthreads();
+            while (ef < e1 && seg_col[ef] + seg_len[ef] <= ch) ++ef;
+            for (int64_t e = ef; e < e1; ++e) {
+                const int sc = seg_col[e];
+                if (sc >= ch + cw) break;
+                const int lo = max(sc, ch), hi = min(sc + seg_len[e], ch + cw);
+                const int64_t so = seg_off[e] + (lo - sc);       // vec offset of the first source
+                for (int j = threadIdx.x; j < hi - lo; j += blockDim.x) {
+                    const int64_t o = so + j;
+                    float w[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k < D; ++k) w[k] = px[k * vlen + (o - v_base)];
+                    if constexpr (NR == 1) {
+                        w[VSLOT] = vec[o * nrhs + c0];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) sv[(lo - ch + j) * NR + c] = vec[o * nrhs + c0 + c];
+                    }
+                    s4[lo - ch + j] = make_float4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            __syncthreads();
+            if (active) {
+                // jb is a multiple of 4 below cw <= TILE, so jb + 3 < TILE
+                for (int jb = part * 4; jb < cw; jb += step) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = jb + q;
+                        const float4 s = s4[j];
+                        const float dx = xi[0] - s.x, dy = xi[1] - s.y;
+                        float r2 = fmaf(dy, dy, dx * dx);
+                        if constexpr (D == 3) {
+                            const float dz = xi[2] - s.z;
+                            r2 = fmaf(dz, dz, r2);
+                        }
+                        const T gk = j < cw ? m2l_kernel<KIND>(r2, param2, diag) : T(0);
+                        if constexpr (NR == 1) {
+                            acc[q][0] = fmaf(gk, D == 3 ? s.w : s.z, acc[q][0]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < NR; ++c) acc[q][c] = fmaf(gk, sv[j * NR + c], acc[q][c]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[0][c] = (acc[0][c] + acc[1][c]) + (acc[2][c] + acc[3][c]);
+        __syncthreads();
+        if (part > 0 && active) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) red[((part - 1) * R + li) * NR + c] = acc[0][c];
+        }
+        __syncthreads();
+        if (part == 0 && active) {
+            for (int p2 = 1; p2 < nparts; ++p2)
+#pragma unroll
+                for (int c = 0; c < NR; ++c) acc[0][c] += red[((p2 - 1) * R + li) * NR + c];
+        }
+        if (part == 0 && active) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) vec[(dst[t] + i) * nrhs + c0 + c] = acc[0][c];
+        }
+    }
+}
+
 // ---- (H2+H)*: t = V^T q_Y per block (partial sums over point chunks) ----------
 template <typename T>
 __global__ void k_lr_vtq(int64_t b0, int64_t nblk, const int64_t* __restrict__ y0,

@@ -117,6 +117,18 @@ def test_bf16_and_tensor_core_options_are_validated():
                                           host_only=True).info()["bytes_m2l"]
 
 
+def test_m2l_on_the_fly_stores_no_coupling_blocks():
+    P = inputs.points(3000, 3, 5)
+    with pytest.raises(H2Error) as e:
+        H2Matrix(P, "invr", leaf_size=32, tol=1e-6, m2l="fly", host_only=True)   # fp64
+    assert e.value.code == -5
+    S = H2Matrix(P, "invr", leaf_size=32, tol=1e-6, storage="f32", host_only=True).info()
+    F = H2Matrix(P, "invr", leaf_size=32, tol=1e-6, storage="f32", m2l="fly", host_only=True).info()
+    assert S["bytes_m2l"] > 0 and F["bytes_m2l"] == 0
+    assert F["m2l_src_coeffs"] == S["m2l_src_coeffs"] and F["vlen"] == S["vlen"]
+    assert F["ranks"] == S["ranks"]
+
+
 def test_near_field_storage_accounting():
     P = inputs.points(4096, 2, 1001)
     S = H2Matrix(P, "log2d", leaf_size=64, tol=1e-6, host_only=True).info()

@@ -229,3 +229,29 @@ def test_converted_handle_equals_a_direct_build(src_near, target, direct_near):
     D = H2Matrix(P, "log2d", leaf_size=32, tol=1e-8, storage=target, near=direct_near)
     assert C.info()["near_stored"] == D.info()["near_stored"]
     assert np.array_equal(C.matvec(q).cpu().numpy(), D.matvec(q).cpu().numpy())
+
+
+@pytest.mark.parametrize("kind,d,variant,nrhs", [("log2d", 2, "h2star", 1), ("invr", 3, "h2star", 1),
+                                                 ("invr", 3, "h2sqrt", 1), ("log2d", 2, "h2plush", 1),
+                                                 ("invr", 3, "h2star", 5)])
+def test_m2l_on_the_fly_matches_the_oracle(kind, d, variant, nrhs):
+    """fp32 storage with M2L evaluated from the pivot coordinates (T_{X,Y} is
+    the kernel matrix between pivots, §3.6.4).  A stored fp32 entry is the fp64
+    value rounded once (u/2); an entry evaluated in fp32 carries the rounding of
+    r^2 (two operations) and of the function (a few ulps), about 4 u, so the
+    bar is 4 x the fp32 bar, against the oracle and against the stored-block
+    fp32 product."""
+    N = 5000
+    P = inputs.points(N, d, 61)
+    Q = inputs.rhs(N, nrhs, 62).reshape(N, nrhs)
+    A = H2Matrix(P, kind, leaf_size=64, tol=1e-8, variant=variant, storage="f32", m2l="fly")
+    B = H2Matrix(P, kind, leaf_size=64, tol=1e-8, variant=variant, storage="f32")
+    assert A.info()["bytes_m2l"] == 0
+    y = A.matvec(_dev(Q)).cpu().numpy().reshape(N, nrhs)
+    z = B.matvec(_dev(Q)).cpu().numpy().reshape(N, nrhs)
+    ref = h2.H2(P, kind, variant=variant, n_max=64, eps=1e-8).matvec(Q).reshape(N, nrhs)
+    bound = 4 * 64 * 2.0 ** -24 * (np.abs(dense.matrix(kind, P)) @ np.abs(Q))
+    r_ref = float((np.abs(y - ref) / bound).max())
+    r_st = float((np.abs(y - z) / bound).max())
+    print(f"m2l fly {kind} {variant} nrhs {nrhs}: {r_ref:.3f} of the bar vs oracle, {r_st:.3f} vs stored")
+    assert r_ref <= 1.0 and r_st <= 1.0
