@@ -51,6 +51,8 @@ extern "C" {
 #define H2_STAR_BT            0   /* H2*(b+t),      §5.1   */
 #define H2_PLUS_H_STAR        1   /* (H2+H)*,       §5.2   */
 #define H2_SQRTD_B            2   /* H2_sqrt(d)(b), App. A */
+#define H2_STAR_T             3   /* H2*(t),        App. C: one basis, T2B NCA over IL_*   */
+#define H2_SQRTD_T            4   /* H2_sqrt(d)(t), App. B: one basis, T2B NCA over IL_sqrt */
 
 /* ---- operator storage precision ------------------------------------------- */
 #define H2_F64                0   /* operators, coefficients and accumulation in fp64 (FP64 pipe) */

@@ -107,7 +107,15 @@ class H2:
             self.lowrank = self._pure_aca(self.eps_ver)
         if variant == "h2sqrt":
             self.bases["far"] = self._b2t(t.il_sqrt, self.eps_far)
-        self.near = t.near_sqrt if variant == "h2sqrt" else t.near_star
+        # App. C, H2*(t): one basis from T2B NCA over the whole IL_*; App. B,
+        # H2_sqrt(d)(t): one basis from T2B NCA over the strong-admissibility lists
+        if variant == "h2star_t":
+            self.bases["far"] = self._t2b(t.il_star, self.eps_far)
+        if variant == "h2sqrt_t":
+            self.bases["far"] = self._t2b(t.il_sqrt, self.eps_far)
+        if variant not in ("h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t"):
+            raise ValueError(f"unknown variant {variant}")
+        self.near = t.near_sqrt if variant in ("h2sqrt", "h2sqrt_t") else t.near_star
         for b in self.bases.values():
             self._operators(b)
         self.kappa = K

@@ -159,6 +159,13 @@ class Tree:
         return [y for y in self.clan(level, key)
                 if classify(c, key_to_coords(y, level, self.d)) == "ver"]
 
+    def il_star(self, level, key):
+        """IL_*(C) = IL_far(C) u IL_ver(C): the clan members that are far-field or
+        vertex-sharing (§3.5), in the clan's (ascending key) order."""
+        c = key_to_coords(key, level, self.d)
+        return [y for y in self.clan(level, key)
+                if classify(c, key_to_coords(y, level, self.d)) in ("far", "ver")]
+
     def il_sqrt(self, level, key):
         if level == 0:
             return []

@@ -605,7 +605,7 @@ void pack(Host& H) {
     struct Copy { const std::vector<double>* src; int64_t dst; int64_t rows, cols, pad; };
     std::vector<Copy> copies;
     const int64_t nleaf = t.nboxes(K);
-    const Csr& NL = (H.variant == 2) ? H.lists.near_sqrt : H.lists.near_star;
+    const Csr& NL = (H.variant == 2 || H.variant == 4) ? H.lists.near_sqrt : H.lists.near_star;
     P.near_ptr = NL.ptr;
     P.near_idx = NL.idx;
     // leaf block rows: [ K(t^X, t^X') for X' in N(X) | U_X^b for each basis ]
@@ -883,6 +883,32 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
         H.bases.emplace_back();
         b2t(H, H.bases.back(), H.lists.sqrtd, H.eps_far);
     }
+    if (H.variant == 3) {
+        // H2*(t) (App. C): one basis, T2B NCA over the whole IL_* = IL_far u IL_ver
+        H.lists.star.assign(H.tree.kappa + 1, Csr());
+        for (int l = 0; l <= H.tree.kappa; ++l) {
+            const Csr &F = H.lists.far[l], &V = H.lists.ver[l];
+            Csr& S = H.lists.star[l];
+            const int64_t n = H.tree.nboxes(l);
+            S.ptr.assign(n + 1, 0);
+            for (int64_t X = 0; X < n; ++X) {
+                // both lists are in ascending key order: merge them
+                int64_t a = F.ptr[X], b = V.ptr[X];
+                while (a < F.ptr[X + 1] || b < V.ptr[X + 1]) {
+                    if (b >= V.ptr[X + 1] || (a < F.ptr[X + 1] && F.idx[a] < V.idx[b])) S.idx.push_back(F.idx[a++]);
+                    else S.idx.push_back(V.idx[b++]);
+                }
+                S.ptr[X + 1] = int64_t(S.idx.size());
+            }
+        }
+        H.bases.emplace_back();
+        t2b(H, H.bases.back(), H.lists.star, H.eps_far);
+    }
+    if (H.variant == 4) {
+        // H2_sqrt(d)(t) (App. B): one basis, T2B NCA over the strong-admissibility lists
+        H.bases.emplace_back();
+        t2b(H, H.bases.back(), H.lists.sqrtd, H.eps_far);
+    }
     tick("pivots");
     for (Basis& B : H.bases) {
         std::string e = operators(H, B);
@@ -904,7 +930,7 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
     tick("pack");
     // near-field work
     const Tree& t = H.tree;
-    const Csr& NL = (H.variant == 2) ? H.lists.near_sqrt : H.lists.near_star;
+    const Csr& NL = (H.variant == 2 || H.variant == 4) ? H.lists.near_sqrt : H.lists.near_star;
     H.near_pairs = 0;
     H.near_evals = 0;
     for (int64_t X = 0; X < t.nboxes(t.kappa); ++X)

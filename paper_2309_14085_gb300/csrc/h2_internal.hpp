@@ -58,6 +58,7 @@ struct Csr {
 // Interaction and near-field lists, per level (§3.5 weak, §3.3 strong).
 struct Lists {
     std::vector<Csr> far, ver, sqrtd;   // [level]
+    std::vector<Csr> star;              // [level] IL_* = IL_far u IL_ver, ascending keys
     Csr near_star, near_sqrt;           // leaf level
 };
 

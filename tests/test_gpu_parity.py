@@ -72,7 +72,7 @@ def _dense_bar(y, ref, exact, eps):
     assert re_gpu <= max(10 * eps, 1.02 * re_orc)
 
 
-@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt"])
+@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t"])
 def test_c1_2d_log_n4096_matches_oracle_and_dense(variant):
     P = inputs.points(4096, 2, 1001)
     q = inputs.rhs(4096, 1, 2001)
@@ -99,7 +99,7 @@ def test_storage_and_near_modes_match_oracle(storage, near):
         _check_mode(y, ref, storage, kind, P, q)
 
 
-@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt"])
+@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t"])
 def test_3d_invr_ragged_matches_oracle(variant):
     """3D, N not a power of two, leaves of varying occupancy (ragged tiles)."""
     P = inputs.points(9000, 3, 77)

@@ -310,7 +310,7 @@ def test_symmetric_reading_gives_transposed_operators(h2star_small):
         np.linalg.norm(H.matvec(c))
 
 
-@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt"])
+@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t"])
 def test_traversal_equals_assembled_matrix(variant):
     """The MVP traversal equals K~ q with K~ written out block by block from the
     same operators (separates traversal mistakes from compression error)."""
@@ -324,7 +324,7 @@ def test_traversal_equals_assembled_matrix(variant):
     assert np.allclose(H.matvec(Q), A @ Q, rtol=0, atol=1e-12 * np.abs(A @ Q).max())
 
 
-@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt"])
+@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t"])
 @pytest.mark.parametrize("kind,d", [("log2d", 2), ("invr", 3)])
 def test_tight_tolerance_matches_dense(variant, kind, d):
     """At eps = 1e-12 the compressed product matches the plain definition to 1e-10."""
