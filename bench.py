@@ -32,7 +32,7 @@ UNIT = "points*RHS/s"
 KERNEL_NAMES = {"log2d": "log r (2D)", "invr": "1/r (3D)", "imq": "inverse multiquadric",
                 "matern12": "exp(-r)"}
 VARIANT_NAMES = {"h2star": "H2*(b+t)", "h2plush": "(H2+H)*", "h2sqrt": "H2_sqrt(d)(b)",
-                 "h2star_t": "H2*(t)", "h2sqrt_t": "H2_sqrt(d)(t)"}
+                 "h2star_t": "H2*(t)", "h2sqrt_t": "H2_sqrt(d)(t)", "h2star_b": "B2T over IL_* (naive)"}
 # DRAM traffic / algorithmic bytes of the M2L block-row launch, from one ncu
 # capture of the current kernel (profiles/k_rowgemv1_m2l_c2s_3d_invr_n32768.md);
 # traffic grows with the stored blocks, so a full launch's traffic is this

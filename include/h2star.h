@@ -53,6 +53,9 @@ extern "C" {
 #define H2_SQRTD_B            2   /* H2_sqrt(d)(b), App. A */
 #define H2_STAR_T             3   /* H2*(t),        App. C: one basis, T2B NCA over IL_*   */
 #define H2_SQRTD_T            4   /* H2_sqrt(d)(t), App. B: one basis, T2B NCA over IL_sqrt */
+#define H2_STAR_B             5   /* B2T NCA over the whole IL_* (§4.1): the construction the
+                                     paper shows to lose accuracy on vertex-sharing clusters;
+                                     built for comparison                                     */
 
 /* ---- operator storage precision ------------------------------------------- */
 #define H2_F64                0   /* operators, coefficients and accumulation in fp64 (FP64 pipe) */

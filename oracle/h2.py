@@ -113,7 +113,11 @@ class H2:
             self.bases["far"] = self._t2b(t.il_star, self.eps_far)
         if variant == "h2sqrt_t":
             self.bases["far"] = self._t2b(t.il_sqrt, self.eps_far)
-        if variant not in ("h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t"):
+        # §4.1: B2T NCA over the whole IL_* (levels kappa .. 1) -- the pivot
+        # strategy the paper shows to lose accuracy on vertex-sharing clusters
+        if variant == "h2star_b":
+            self.bases["far"] = self._b2t(t.il_star, self.eps_far, lmin=1)
+        if variant not in ("h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t", "h2star_b"):
             raise ValueError(f"unknown variant {variant}")
         self.near = t.near_sqrt if variant in ("h2sqrt", "h2sqrt_t") else t.near_star
         for b in self.bases.values():
@@ -124,12 +128,12 @@ class H2:
         return kernels.block(self.kind, self.P, rows, cols, self.param)
 
     # ---- pivot selection --------------------------------------------------
-    def _b2t(self, il, eps):
-        """B2T NCA (Algorithm 1) over the lists `il`, levels kappa .. 2."""
+    def _b2t(self, il, eps, lmin=2):
+        """B2T NCA (Algorithm 1) over the lists `il`, levels kappa .. lmin."""
         t, K = self.tree, self.tree.kappa
-        b = Basis("far", 2, K)
+        b = Basis("far", lmin, K)
         empty = np.zeros(0, dtype=np.int64)
-        for l in range(K, 1, -1):
+        for l in range(K, lmin - 1, -1):
             for X in range(t.nboxes(l)):
                 Ys = il(l, X)
                 b.il[(l, X)] = Ys

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libh2star.so")
 
 KERNELS = {"log2d": 0, "invr": 1, "imq": 2, "matern12": 3}
-VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2, "h2star_t": 3, "h2sqrt_t": 4}
+VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2, "h2star_t": 3, "h2sqrt_t": 4, "h2star_b": 5}
 STORAGE = {"f64": 0, "f32": 1, "df64": 2, "bf16": 3}
 NEAR = {None: 0, "fly": 1, "stored": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")

@@ -785,7 +785,7 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     if (kernel < 0 || kernel > 3) return fail(H2_E_INVALID_ARG, "unknown kernel");
     if (leaf_size < 1) return fail(H2_E_INVALID_ARG, "leaf_size must be >= 1");
     if (!(tol > 0.0 && tol < 1.0)) return fail(H2_E_INVALID_ARG, "tol must be in (0, 1)");
-    if (variant < 0 || variant > 4) return fail(H2_E_INVALID_ARG, "unknown variant");
+    if (variant < 0 || variant > 5) return fail(H2_E_INVALID_ARG, "unknown variant");
     h2_build_opts o;
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;

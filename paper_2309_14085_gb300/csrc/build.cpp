@@ -381,15 +381,15 @@ void lu_solve(const std::vector<double>& A, int n, const std::vector<int>& piv, 
 
 // ---------------------------------------------------------------------------
 // Pivot selection
-void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps) {
+void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps, int lmin = 2) {
     const Tree& t = H.tree;
     const int K = t.kappa, d = t.d;
-    B.lmin = 2;
+    B.lmin = lmin;
     B.il = &il;
     B.tau.assign(K + 1, {});
     B.sig.assign(K + 1, {});
     for (int l = 0; l <= K; ++l) { B.tau[l].resize(t.nboxes(l)); B.sig[l].resize(t.nboxes(l)); }
-    for (int l = K; l >= 2; --l) {
+    for (int l = K; l >= lmin; --l) {
         const int64_t n = t.nboxes(l);
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t X = 0; X < n; ++X) {
@@ -883,8 +883,8 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
         H.bases.emplace_back();
         b2t(H, H.bases.back(), H.lists.sqrtd, H.eps_far);
     }
-    if (H.variant == 3) {
-        // H2*(t) (App. C): one basis, T2B NCA over the whole IL_* = IL_far u IL_ver
+    if (H.variant == 3 || H.variant == 5) {
+        // IL_* = IL_far u IL_ver per box
         H.lists.star.assign(H.tree.kappa + 1, Csr());
         for (int l = 0; l <= H.tree.kappa; ++l) {
             const Csr &F = H.lists.far[l], &V = H.lists.ver[l];
@@ -902,7 +902,10 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
             }
         }
         H.bases.emplace_back();
-        t2b(H, H.bases.back(), H.lists.star, H.eps_far);
+        if (H.variant == 3)   // H2*(t) (App. C): one basis, T2B NCA over the whole IL_*
+            t2b(H, H.bases.back(), H.lists.star, H.eps_far);
+        else                  // §4.1: B2T NCA over the whole IL_*, levels kappa .. 1
+            b2t(H, H.bases.back(), H.lists.star, H.eps_far, 1);
     }
     if (H.variant == 4) {
         // H2_sqrt(d)(t) (App. B): one basis, T2B NCA over the strong-admissibility lists

@@ -147,7 +147,7 @@ def test_matvec_on_host_only_handle_is_rejected():
     assert A.info()["bytes_device"] == 0
 
 
-@pytest.mark.parametrize("variant", ["h2star", "h2sqrt", "h2plush", "h2star_t", "h2sqrt_t"])
+@pytest.mark.parametrize("variant", ["h2star", "h2sqrt", "h2plush", "h2star_t", "h2sqrt_t", "h2star_b"])
 @pytest.mark.parametrize("kind,d,N,n_max,eps", [("log2d", 2, 4096, 64, 1e-8),
                                                 ("invr", 3, 6000, 32, 1e-6),
                                                 ("imq", 2, 3000, 32, 1e-8)])

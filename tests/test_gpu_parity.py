@@ -99,7 +99,7 @@ def test_storage_and_near_modes_match_oracle(storage, near):
         _check_mode(y, ref, storage, kind, P, q)
 
 
-@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t"])
+@pytest.mark.parametrize("variant", ["h2star", "h2plush", "h2sqrt", "h2star_t", "h2sqrt_t", "h2star_b"])
 def test_3d_invr_ragged_matches_oracle(variant):
     """3D, N not a power of two, leaves of varying occupancy (ragged tiles)."""
     P = inputs.points(9000, 3, 77)

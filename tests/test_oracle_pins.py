@@ -384,3 +384,27 @@ def test_gmres_with_compressed_operator_re_sol():
     b = q + dense.product("log2d", P, q) / 1500.0
     x, hist, it = gmres.gmres(op, b, rtol=1e-12, maxit=100)
     assert np.linalg.norm(x - q) / np.linalg.norm(q) < 1e-8
+
+
+def test_b2t_over_the_weak_admissibility_loses_accuracy_and_t2b_does_not():
+    """§4's central observation, reproduced at a small size: with far-field and
+    vertex-sharing clusters both admissible, B2T NCA over the whole list leaves
+    a matrix error many orders of magnitude above eps, T2B NCA (H2*(t)) stays
+    at eps, and the proposed H2*(b+t) (B2T far field, T2B vertex-sharing) too.
+    The paper's values (1/r, N = 160000, n_max = 400) are in
+    tests/golden/paper_b2t_vs_t2b.txt: a gap of 6 orders at eps = 1e-10; here
+    2D, N = 4096, n_max = 32 (Frobenius norm, to keep the test cheap)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "paper_b2t_vs_t2b.txt"))
+            if l.strip() and not l.startswith("#")]
+    paper = {float(r[0]): (float(r[1]), float(r[2])) for r in rows}
+    eps = 1e-10
+    assert paper[eps][0] / paper[eps][1] > 1e5
+    P = inputs.points(4096, 2, 77)
+    K = dense.matrix("invr", P)
+    nK = np.linalg.norm(K)
+    re = {v: np.linalg.norm(K - h2.H2(P, "invr", variant=v, n_max=32, eps=eps).dense()) / nK
+          for v in ("h2star_b", "h2star_t", "h2star")}
+    assert re["h2star_t"] <= 10 * eps
+    assert re["h2star"] <= 100 * eps
+    assert re["h2star_b"] >= 1e4 * re["h2star_t"]
+    assert re["h2star_b"] >= 1e3 * re["h2star"]
