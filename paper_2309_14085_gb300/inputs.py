@@ -92,3 +92,12 @@ def poisson_arrivals(count, rate, ngeom, seed=4999):
     t = np.cumsum(rng.exponential(1.0 / rate, size=count))
     g = rng.integers(0, ngeom, size=count)
     return t - t[0], g
+
+
+def chebyshev_grid(n, d):
+    """The n^d tensor grid of Chebyshev points cos(pi (2i + 1) / (2n)), i < n, in
+    [-1, 1]^d: the non-uniform point sets of the paper's Chebyshev experiments
+    (dense near the faces, sparse in the middle), in lexicographic order."""
+    x = np.cos(np.pi * (2 * np.arange(n) + 1) / (2 * n))
+    g = np.meshgrid(*([x] * d), indexing="ij")
+    return np.stack([a.ravel() for a in g], axis=1)

@@ -255,3 +255,19 @@ def test_m2l_on_the_fly_matches_the_oracle(kind, d, variant, nrhs):
     r_st = float((np.abs(y - z) / bound).max())
     print(f"m2l fly {kind} {variant} nrhs {nrhs}: {r_ref:.3f} of the bar vs oracle, {r_st:.3f} vs stored")
     assert r_ref <= 1.0 and r_st <= 1.0
+
+
+@pytest.mark.parametrize("variant", ["h2star", "h2star_t"])
+def test_chebyshev_grid_matern_matches_oracle(variant):
+    """A non-uniform point set on the uniform octree (the paper's Chebyshev-grid
+    experiments): 18^3 Chebyshev points, Matérn nu = 1/2 (exp(-r)), many boxes
+    nearly empty.  fp64 bar against the oracle, dense bar as elsewhere."""
+    P = inputs.chebyshev_grid(18, 3)
+    N = P.shape[0]
+    q = inputs.rhs(N, 1, 71)
+    A = H2Matrix(P, "matern12", leaf_size=32, tol=1e-8, variant=variant)
+    y = _gpu_mvp(A, q)
+    O = h2.H2(P, "matern12", variant=variant, n_max=32, eps=1e-8)
+    ref = O.matvec(q)
+    assert _maxrel(y, ref) <= F64_TOL
+    _dense_bar(y, ref, dense.product("matern12", P, q), 1e-8)
