@@ -53,6 +53,7 @@ struct DevRowTasks {
     int64_t n = 0;
     size_t smem = 0;
     int rw = 4;                   // rows per warp (autotuned for the large lists)
+    int max_rows = 0;             // largest task (rows)
     int64_t *dst = nullptr, *aoff = nullptr, *seg_ptr = nullptr, *seg_off = nullptr;
     int32_t *rows = nullptr, *kpad = nullptr, *seg_len = nullptr, *seg_col = nullptr;
 };
@@ -219,22 +220,55 @@ int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize
     H2_TRY(dev_upload(h, &D.seg_len, R.seg_len));
     H2_TRY(dev_upload(h, &D.seg_col, R.seg_col));
     D.smem = 0;
+    D.max_rows = R.rows.empty() ? 0 : *std::max_element(R.rows.begin(), R.rows.end());
     (void)vsize;
     return H2_OK;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
+// Rows per CTA: the whole task, or -- for a list with fewer tasks than 4 CTAs
+// per SM (the coarse levels) -- chunks of whole 8 x RW-row passes, one CTA per
+// chunk along y, until the list has about that many CTAs.  Every row is still
+// computed by one warp in the same order.
+void row_split(const DevRowTasks& R, int rw, unsigned* gy, int* chunk) {
+    const int pass = 8 * rw;
+    const int64_t target = 4 * int64_t(sm_count());
+    *gy = 1;
+    *chunk = 1 << 30;
+    if (R.n >= target || R.max_rows <= pass) return;
+    const int passes = (R.max_rows + pass - 1) / pass;
+    const int want = int(std::min<int64_t>(passes, (target + R.n - 1) / R.n));
+    const int per = (passes + want - 1) / want;          // passes per CTA
+    *chunk = per * pass;
+    *gy = unsigned((R.max_rows + *chunk - 1) / *chunk);
 }
 
 template <class A, int RW, int NR>
 void launch_rows_rw(const DevRowTasks& R, const void* ops, void* vec, cudaStream_t s, int accumulate,
                     int nrhs, int c0) {
+    unsigned gy = 1;
+    int chunk = 1 << 30;
+    row_split(R, RW, &gy, &chunk);
+    const dim3 grid(unsigned(R.n), gy);
     if (NR == 1 && nrhs == 1)
-        h2::k_rowgemv1<A, RW><<<unsigned(R.n), 256, 0, s>>>(
-                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
-                static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate);
-    else
-        h2::k_rowgemv<A, RW, NR><<<unsigned(R.n), 256, 0, s>>>(
+        h2::k_rowgemv1<A, RW><<<grid, 256, 0, s>>>(
                 R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
                 static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate,
-                nrhs, c0);
+                chunk);
+    else
+        h2::k_rowgemv<A, RW, NR><<<grid, 256, 0, s>>>(
+                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col,
+                static_cast<const typename A::S*>(ops), static_cast<typename A::V*>(vec), accumulate,
+                nrhs, c0, chunk);
 }
 
 // Largest RHS tile: 4 columns in fp32, 2 in fp64 / double-float.  Wider tiles
@@ -1534,6 +1568,7 @@ int bupload_rows(h2_batch b, DevRowTasks& D, const h2::RowTasks& R) {
     H2_TRY(bupload(b, &D.seg_len, R.seg_len));
     H2_TRY(bupload(b, &D.seg_col, R.seg_col));
     D.rw = 4;
+    D.max_rows = R.rows.empty() ? 0 : *std::max_element(R.rows.begin(), R.rows.end());
     return H2_OK;
 }
 

@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_rowgemv(
     const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
     const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
     const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate,
-    int nrhs, int c0) {
+    int nrhs, int c0, int row_chunk) {
     using V = typename A::V;
     using L = typename A::L;
     constexpr int W = A::W;
@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(256) k_rowgemv(
     const typename A::S* Am = ops + aoff[t];
     V* y = vec + dst[t] * nrhs + c0;
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-    for (int r0 = 0; r0 < nr; r0 += NW * RW) {
+    const int rb0 = int(blockIdx.y) * row_chunk, rb1 = min(nr, rb0 + row_chunk);
+    for (int r0 = rb0; r0 < rb1; r0 += NW * RW) {
         V acc[RW][NR];
         bool ok[RW];
         const L* arow[RW];
@@ -384,7 +385,8 @@ __global__ void __launch_bounds__(256) k_rowgemv1(
     const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
     const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
     const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
-    const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate) {
+    const typename A::S* __restrict__ ops, typename A::V* __restrict__ vec, int accumulate,
+    int row_chunk) {
     using V = typename A::V;
     using L = typename A::L;
     constexpr int W = A::W;
@@ -401,7 +403,8 @@ __global__ void __launch_bounds__(256) k_rowgemv1(
     const typename A::S* Am = ops + aoff[t];
     V* y = vec + dst[t];
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-    for (int r0 = 0; r0 < nr; r0 += NW * RW) {
+    const int rb0 = int(blockIdx.y) * row_chunk, rb1 = min(nr, rb0 + row_chunk);
+    for (int r0 = rb0; r0 < rb1; r0 += NW * RW) {
         V acc[RW];
         bool ok[RW];
         const L* arow[RW];
