@@ -51,7 +51,6 @@ enum Stage { ST_GATHER, ST_P2M, ST_M2M, ST_M2L, ST_L2L, ST_LEAF, ST_LOWRANK, ST_
 // Device copy of one block-row task list.
 struct DevRowTasks {
     int64_t n = 0;
-    size_t smem = 0;
     int rw = 4;                   // rows per warp (autotuned for the large lists)
     int max_rows = 0;             // largest task (rows)
     int64_t *dst = nullptr, *aoff = nullptr, *seg_ptr = nullptr, *seg_off = nullptr;
@@ -209,7 +208,7 @@ int grow_vec(h2_handle h, int nrhs) {
     return H2_OK;
 }
 
-int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize) {
+int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R) {
     D.n = R.size();
     H2_TRY(dev_upload(h, &D.dst, R.dst));
     H2_TRY(dev_upload(h, &D.aoff, R.aoff));
@@ -219,9 +218,7 @@ int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R, size_t vsize
     H2_TRY(dev_upload(h, &D.kpad, R.kpad));
     H2_TRY(dev_upload(h, &D.seg_len, R.seg_len));
     H2_TRY(dev_upload(h, &D.seg_col, R.seg_col));
-    D.smem = 0;
     D.max_rows = R.rows.empty() ? 0 : *std::max_element(R.rows.begin(), R.rows.end());
-    (void)vsize;
     return H2_OK;
 }
 
@@ -497,14 +494,14 @@ int upload(h2_handle h) {
     H2_TRY(dev_upload(h, &h->uoff, P.uoff));
     H2_TRY(dev_upload(h, &h->ustride, P.ustride));
     H2_TRY(dev_upload(h, &h->utoff, P.utoff));
-    H2_TRY(upload_rows(h, h->p2m, P.p2m, sizeof(V)));
-    H2_TRY(upload_rows(h, h->m2l, P.m2l, sizeof(V)));
-    H2_TRY(upload_rows(h, h->leaf, P.leaf, sizeof(V)));
+    H2_TRY(upload_rows(h, h->p2m, P.p2m));
+    H2_TRY(upload_rows(h, h->m2l, P.m2l));
+    H2_TRY(upload_rows(h, h->leaf, P.leaf));
     h->m2m.assign(t.kappa + 1, DevRowTasks());
     h->l2l.assign(t.kappa + 1, DevRowTasks());
     for (int l = 0; l <= t.kappa; ++l) {
-        H2_TRY(upload_rows(h, h->m2m[l], P.m2m[l], sizeof(V)));
-        H2_TRY(upload_rows(h, h->l2l[l], P.l2l[l], sizeof(V)));
+        H2_TRY(upload_rows(h, h->m2m[l], P.m2m[l]));
+        H2_TRY(upload_rows(h, h->l2l[l], P.l2l[l]));
     }
     // (H2+H)* groups: consecutive blocks of one level with the same target box
     const int64_t nblk = int64_t(P.lr_k.size());
