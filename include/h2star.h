@@ -11,8 +11,12 @@
  *   - (H2+H)*       (§5.2): the same far field plus one ACA per vertex-sharing
  *                           pair (Algorithms 3 and 4);
  *   - H2_sqrt(d)(b) (App. A): standard far-field H2, one basis from B2T NCA;
+ *   - H2*(t), H2_sqrt(d)(t) (App. C, App. B): one basis from T2B NCA over the
+ *                           whole weak / strong admissibility lists;
  * and applies it on the GPU (upward pass, coupling products, downward pass and
- * the near field evaluated on the fly, §5.1.2).
+ * the near field, §5.1.2).  Solves (GMRES with mixed-precision refinement),
+ * batched products over many trees and a continuous-batching solve server sit
+ * on top of the same products.
  *
  * Conventions for every entry point:
  *   - the return value is H2_OK (0) or a negative H2_E_* code; the message of
@@ -149,7 +153,8 @@ int h2_release_host(h2_handle h);
 int h2_convert(h2_handle src, int storage, h2_handle* out);
 
 /*
- * h2_matvec -- Y = K~ X for nrhs right-hand sides (§5.1.2 / §5.2.2 / App. A.2).
+ * h2_matvec -- Y = K~ X for nrhs right-hand sides (§5.1.2 / §5.2.2 / App. A.2,
+ * App. B.2 and App. C.2 for the T2B-only variants).
  *
  *   X      device, fp64, column-major N x nrhs with leading dimension ldx >= N,
  *          rows in the user's point order (the order of `points`).
@@ -161,9 +166,15 @@ int h2_convert(h2_handle src, int storage, h2_handle* out);
  * Every step runs in this library's CUDA kernels: gather into tree order,
  * P2M, M2M, M2L (far and vertex-sharing), L2L, L2P fused with the near field
  * (evaluated on the fly from the coordinates, or from stored kernel blocks,
- * per h2_build_opts.near_mode), scatter back.  Precision follows the build's
- * storage (H2_F64, H2_F32 or H2_DF64).
- * Errors: H2_E_INVALID_ARG, H2_E_NO_DEVICE (host-only handle), H2_E_CUDA.
+ * per h2_build_opts.near_mode), scatter back; with h2_build_opts.m2l_mode = 1
+ * the M2L blocks are evaluated from the pivot coordinates.  Precision follows
+ * the build's storage (H2_F64, H2_F32, H2_DF64 or H2_BF16); RHS tiles of 16-64
+ * columns run on the tensor cores for H2_BF16 and for H2_F32 built with
+ * tensor_cores = 1.  Each column of a multi-RHS product equals the single-RHS
+ * product of that column bit for bit, except columns run on the tensor cores.
+ * Errors: H2_E_INVALID_ARG (also: the handle serves a solve server),
+ * H2_E_NO_DEVICE (host-only handle), H2_E_CUDA (also: a tensor-core product
+ * of an earlier call gave up waiting for its MMAs).
  */
 int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
               int nrhs, void* stream);
