@@ -44,6 +44,8 @@ extern "C" {
 #define H2_E_NOT_CONVERGED   -4   /* iterative solve stopped at maxit                 */
 #define H2_E_UNSUPPORTED     -5   /* valid request this build does not implement      */
 #define H2_E_NO_DEVICE       -6   /* no CUDA device, or the handle was built host-only */
+#define H2_E_TIMEOUT         -7   /* a bounded device wait expired (the kernel recorded it,
+                                     released its resources and returned)              */
 
 /* ---- kernel functions G(r) (diagonal value in brackets) -------------------- */
 #define H2_KERNEL_LOG2D       0   /* log r      [0]  single-layer Laplace 2D, §6.1.1   */
@@ -173,8 +175,9 @@ int h2_convert(h2_handle src, int storage, h2_handle* out);
  * tensor_cores = 1.  Each column of a multi-RHS product equals the single-RHS
  * product of that column bit for bit, except columns run on the tensor cores.
  * Errors: H2_E_INVALID_ARG (also: the handle serves a solve server),
- * H2_E_NO_DEVICE (host-only handle), H2_E_CUDA (also: a tensor-core product
- * of an earlier call gave up waiting for its MMAs).
+ * H2_E_NO_DEVICE (host-only handle), H2_E_CUDA, H2_E_TIMEOUT (a tensor-core
+ * product of an earlier call gave up waiting for its MMAs: every later call on
+ * the handle returns it).
  */
 int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
               int nrhs, void* stream);

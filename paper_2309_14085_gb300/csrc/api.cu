@@ -966,7 +966,7 @@ int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
         if (rc != H2_OK) return rc;
     }
     if (h->tc_err_host && *h->tc_err_host)
-        return fail(H2_E_CUDA, "a tensor-core product gave up waiting for its MMAs");
+        return fail(H2_E_TIMEOUT, "a tensor-core product gave up waiting for its MMAs");
     return matvec_dispatch(h, X, ldx, Y, ldy, nrhs, s);
 }
 
