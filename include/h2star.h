@@ -291,7 +291,8 @@ typedef struct {
  *          bounds the GMRES iterations over all cycles and refinements.
  *   st     nullable; filled also on H2_E_NOT_CONVERGED (x then holds the last
  *          iterate).  The call synchronises `stream`.
- * Errors: H2_E_INVALID_ARG, H2_E_NO_DEVICE, H2_E_OOM, H2_E_CUDA, H2_E_NOT_CONVERGED.
+ * Errors: H2_E_INVALID_ARG, H2_E_NO_DEVICE, H2_E_OOM, H2_E_CUDA, H2_E_NOT_CONVERGED,
+ * H2_E_TIMEOUT (as for h2_matvec, for h or h_res).
  */
 int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale, const double* b,
              double* x, double rtol, int restart, int maxit, h2_gmres_stats* st, void* stream);
@@ -321,6 +322,25 @@ int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale, const dou
  * H2_E_NO_DEVICE, H2_E_CUDA.
  */
 int h2_matvec_noalloc(h2_handle h, const double* x, double* y, void* stream);
+
+/*
+ * h2_inject_wait_expiry -- failure injection without a GPU fault (the paper
+ * has no counterpart).  Every mbarrier wait of the tensor-core products is
+ * bounded: on expiry the kernel records it in the handle's device error flag,
+ * lets its MMAs in flight finish, frees its TMEM and returns, and the host
+ * reports H2_E_TIMEOUT.  This call runs that path on demand: one warp
+ * allocates TMEM, waits at most `rounds` try_wait rounds (0 <= rounds <= 2^22)
+ * on an mbarrier that nothing arrives on, sets the flag, frees its TMEM and
+ * returns; the flag is then read back on `stream` (asynchronous).  Once the
+ * stream has reached that point, every product on h (h2_matvec,
+ * h2_matvec_noalloc, h2_gmres, a solve server's products) returns
+ * H2_E_TIMEOUT; the device context and other handles stay usable.
+ * Errors: H2_E_INVALID_ARG (NULL handle, rounds out of range, a handle that
+ * serves a solve server), H2_E_NO_DEVICE, H2_E_UNSUPPORTED (the handle runs no
+ * tensor-core products: storage other than H2_BF16 and H2_F32 with
+ * tensor_cores), H2_E_CUDA.
+ */
+int h2_inject_wait_expiry(h2_handle h, int64_t rounds, void* stream);
 
 /* ---- batched products over many independent trees ------------------------ */
 typedef struct h2_batch_s* h2_batch;
@@ -441,7 +461,7 @@ int h2_server_create(const h2_handle* geoms, const h2_handle* res_geoms, int nge
  * residual rtol within maxit iterations.  f: host, N fp64 in user order, copied
  * before the call returns.  *ticket identifies the request.  Non-blocking.
  * Errors: H2_E_INVALID_ARG, H2_E_OOM (workspace larger than the whole budget),
- * H2_E_CUDA (the server stopped after a device error).
+ * H2_E_CUDA or H2_E_TIMEOUT (the server stopped after that device error).
  */
 int h2_server_submit(h2_server s, int geom, double shift, double scale, const double* f,
                      double rtol, int maxit, int64_t* ticket);
@@ -450,7 +470,9 @@ int h2_server_submit(h2_server s, int geom, double shift, double scale, const do
  * h2_server_wait -- block until the request is done; x (host, N, nullable)
  * receives the solution and st (nullable) its statistics.  Each ticket is
  * waited for once.  Returns H2_E_NOT_CONVERGED (x and st still filled) when
- * maxit ran out.  Errors: H2_E_INVALID_ARG (unknown ticket).
+ * maxit ran out, and the error of a product that stopped the request
+ * (H2_E_CUDA, H2_E_TIMEOUT; st->converged = 0).  Errors: H2_E_INVALID_ARG
+ * (unknown ticket).
  */
 int h2_server_wait(h2_server s, int64_t ticket, double* x, h2_request_stats* st);
 

@@ -27,7 +27,8 @@ STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
 EXPORTED = ("h2_build", "h2_convert", "h2_release_host", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
             "h2_batch_matvec", "h2_batch_info", "h2_batch_destroy", "h2_server_create",
-            "h2_server_submit", "h2_server_wait", "h2_server_stats_get", "h2_server_destroy")
+            "h2_server_submit", "h2_server_wait", "h2_server_stats_get", "h2_server_destroy",
+            "h2_inject_wait_expiry")
 
 
 class BuildOpts(ctypes.Structure):
@@ -93,10 +94,16 @@ class RequestStats(ctypes.Structure):
                 ("queue_seconds", ctypes.c_double), ("latency_seconds", ctypes.c_double)]
 
 
+#: Status codes of the C ABI (the H2_OK / H2_E_* defines of h2star.h).
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED",
+          -5: "UNSUPPORTED", -6: "NO_DEVICE", -7: "TIMEOUT"}
+
+
 class H2Error(RuntimeError):
     def __init__(self, code, msg):
-        super().__init__(f"h2 error {code}: {msg}")
+        super().__init__(f"h2 error {code} ({STATUS.get(code, '?')}): {msg}")
         self.code = code
+        self.status = STATUS.get(code)
 
 
 _lib = None
@@ -129,6 +136,7 @@ def lib():
         L.h2_batch_destroy.restype = None
         L.h2_convert.argtypes = [c_vp, c_int, ctypes.POINTER(c_vp)]
         L.h2_release_host.argtypes = [c_vp]
+        L.h2_inject_wait_expiry.argtypes = [c_vp, c_i64, c_vp]
         L.h2_server_create.argtypes = [c_vp, c_vp, c_int, ctypes.POINTER(ServerOpts),
                                        ctypes.POINTER(c_vp)]
         L.h2_server_submit.argtypes = [c_vp, c_int, c_dbl, c_dbl, c_vp, c_dbl, c_int,
@@ -229,6 +237,12 @@ class H2Matrix:
         if out is not None:
             return out
         return Y.reshape(self.N) if vec else Y
+
+    def inject_wait_expiry(self, rounds=1 << 12, stream=None):
+        """Run the expiry path of the tensor-core kernels' bounded waits (no GPU
+        fault): afterwards every product on this matrix raises H2Error with
+        status TIMEOUT.  Asynchronous on `stream`."""
+        _check(lib().h2_inject_wait_expiry(self._h, rounds, _stream_ptr(stream)))
 
     # -- solves ------------------------------------------------------------------
     def gmres(self, b, shift=0.0, scale=1.0, rtol=1e-10, restart=100, maxit=1000,

@@ -778,6 +778,9 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
 // the pipeline in the handle's storage
 int matvec_dispatch(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int nrhs,
                     cudaStream_t s) {
+    // the flag of an earlier tensor-core product (read back after each one)
+    if (h->tc_err_host && *h->tc_err_host)
+        return fail(H2_E_TIMEOUT, "a tensor-core product gave up waiting for its MMAs");
     switch (h->host.storage) {
         case H2_F64: return matvec_one<h2::F64>(h, X, ldx, Y, ldy, nrhs, s);
         case H2_F32: return matvec_one<h2::F32>(h, X, ldx, Y, ldy, nrhs, s);
@@ -965,9 +968,22 @@ int h2_matvec(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy,
         int rc = next_event_set(h);
         if (rc != H2_OK) return rc;
     }
-    if (h->tc_err_host && *h->tc_err_host)
-        return fail(H2_E_TIMEOUT, "a tensor-core product gave up waiting for its MMAs");
     return matvec_dispatch(h, X, ldx, Y, ldy, nrhs, s);
+}
+
+extern "C" int h2_inject_wait_expiry(h2_handle h, int64_t rounds, void* stream) {
+    g_err.clear();
+    if (!h) return fail(H2_E_INVALID_ARG, "NULL handle");
+    if (rounds < 0 || rounds > int64_t(h2::tc::kWaitLimit))
+        return fail(H2_E_INVALID_ARG, "rounds must be in [0, 2^22]");
+    if (!h->on_device) return fail(H2_E_NO_DEVICE, "handle was built host-only");
+    if (h->server) return fail(H2_E_INVALID_ARG, "the handle serves a solve server");
+    if (!h->tc_err) return fail(H2_E_UNSUPPORTED, "the handle runs no tensor-core products");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h2::k_wait_expiry<<<1, 32, 0, s>>>(uint32_t(rounds), h->tc_err);
+    H2_CUDA(cudaGetLastError());
+    H2_CUDA(cudaMemcpyAsync(h->tc_err_host, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return H2_OK;
 }
 
 int h2_info(h2_handle h, h2_stats* st) {
@@ -1861,6 +1877,8 @@ struct Req {
                                            // admission rule, 2 after a fallback
     double beta = 0, beta_prev = 0, bnorm = 0, est = 1, relres = 1;
     bool done = false, converged = false, xzero = true;
+    int rc = H2_OK;                        // status of a product that stopped the request
+    std::string err;
     std::vector<double> H, cs, sn, gv, h1;
 };
 
@@ -1892,6 +1910,7 @@ struct h2_server_s {
     bool stop = false;
     std::thread worker;
     std::string worker_error;
+    int worker_rc = H2_OK;
     h2_server_stats stats = {};           // admission counters (under mu)
     std::atomic<int64_t> ticks{0}, products{0}, product_columns{0};
 
@@ -2178,7 +2197,13 @@ void serve_loop(h2_server S) {
             if (rc != H2_OK) {
                 std::lock_guard<std::mutex> lk(S->mu);
                 S->worker_error = h2_last_error();
-                for (Req* r : act) { r->done = true; r->converged = false; }
+                S->worker_rc = rc;
+                for (Req* r : run) {
+                    r->done = true;
+                    r->converged = false;
+                    r->rc = rc;
+                    r->err = S->worker_error;
+                }
             }
         }
         // retire finished requests
@@ -2330,7 +2355,7 @@ extern "C" int h2_server_submit(h2_server S, int geom, double shift, double scal
     r->t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (!S->worker_error.empty()) return fail(H2_E_CUDA, "server stopped: " + S->worker_error);
+        if (!S->worker_error.empty()) return fail(S->worker_rc, "server stopped: " + S->worker_error);
         Req* raw = r.release();
         raw->id = S->next_id++;
         *ticket = raw->id;
@@ -2366,6 +2391,7 @@ extern "C" int h2_server_wait(h2_server S, int64_t ticket, double* x, h2_request
         st->queue_seconds = r->t_admit - r->t_submit;
         st->latency_seconds = r->t_done - r->t_submit;
     }
+    if (r->rc != H2_OK) return fail(r->rc, "request stopped by a device error: " + r->err);
     if (!r->converged) return fail(H2_E_NOT_CONVERGED, "request stopped before reaching rtol");
     return H2_OK;
 }

@@ -357,4 +357,26 @@ __global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
     }
 }
 
+// The expiry path of the bounded waits above, without a fault: one warp
+// allocates TMEM, waits at most `rounds` try_wait rounds on an mbarrier that
+// nothing arrives on, records kErrTimeout in *err, frees its TMEM and returns.
+// Launch: one block of 32 threads, no dynamic shared memory.
+__global__ void __launch_bounds__(32, 1) k_wait_expiry(uint32_t rounds, int* __restrict__ err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    tc::tmem_alloc(&tmem_slot, 32);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_async_smem();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, rounds)) atomicExch(err, tc::kErrTimeout);
+    __syncthreads();
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 32);
+}
+
 }  // namespace h2

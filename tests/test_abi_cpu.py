@@ -38,6 +38,14 @@ def test_library_exports_every_declared_symbol():
     assert set(pkg.EXPORTED) <= names
 
 
+def test_status_names_match_the_header():
+    text = open(os.path.join(ROOT, "include", "h2star.h")).read()
+    codes = {int(v): n for n, v in re.findall(r"^#define\s+H2_(?:E_)?(\w+)\s+(-?\d+)\b", text, re.M)
+             if n in set(pkg.STATUS.values())}
+    assert codes == pkg.STATUS
+    assert H2Error(-7, "x").status == "TIMEOUT"
+
+
 def test_invalid_arguments_return_error_codes():
     P = inputs.points(100, 2, 1)
     with pytest.raises(H2Error) as e:
@@ -145,6 +153,17 @@ def test_matvec_on_host_only_handle_is_rejected():
     rc = pkg.lib().h2_matvec(A._h, ctypes.c_void_p(16), 300, ctypes.c_void_p(16), 300, 1, None)
     assert rc == -6
     assert A.info()["bytes_device"] == 0
+
+
+def test_wait_expiry_injection_validates_before_any_launch():
+    L = pkg.lib()
+    assert L.h2_inject_wait_expiry(None, 16, None) == -1
+    A = H2Matrix(inputs.points(300, 2, 2), "log2d", leaf_size=16, tol=1e-6, storage="bf16",
+                 host_only=True)
+    assert L.h2_inject_wait_expiry(A._h, -1, None) == -1
+    assert L.h2_inject_wait_expiry(A._h, (1 << 22) + 1, None) == -1
+    assert L.h2_inject_wait_expiry(A._h, 16, None) == -6
+    assert pkg.STATUS[-6] == "NO_DEVICE"
 
 
 @pytest.mark.parametrize("variant", ["h2star", "h2sqrt", "h2plush", "h2star_t", "h2sqrt_t", "h2star_b"])
