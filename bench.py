@@ -172,7 +172,8 @@ def bench_ours(args, rank, world):
                  variant=args.variant, storage=args.storage,
                  tensor_cores=bool(args.tensor_cores) and args.storage == "f32",
                  near="stored" if args.tensor_cores else None,
-                 m2l="fly" if (args.m2l == "fly" and args.storage == "f32") else None)
+                 m2l="fly" if (args.m2l == "fly" and args.storage == "f32") else
+                 ("device" if args.m2l == "device" else None))
     build_s = time.perf_counter() - t0
     info = A.info()
     q = torch.tensor(w["q"].reshape(N, nrhs), dtype=torch.float64, device=dev)
@@ -251,7 +252,7 @@ def bench_ours(args, rank, world):
     hbm, how = _peaks()
     roof = {"kernel": dom, "dominant_stage": dom_all, "stage_ms": {k: round(v, 4) for k, v in per.items()},
             "profiled_ms_per_step": round(prof_ms_step, 4)}
-    if dom == "m2l" and info["m2l_fly"]:
+    if dom == "m2l" and info["m2l_fly"] == 1:
         # M2L from the pivot coordinates: one kernel evaluation (one MUFU rsqrt /
         # lg2) per entry per RHS tile; peak 16 MUFU ops / clock / SM x 152 SMs x
         # 2.07 GHz
@@ -295,7 +296,7 @@ def bench_ours(args, rank, world):
                    "kernel": KERNEL_NAMES[w["kernel"]], "leaf_size": w["n_max"],
                    "kappa": info["kappa"], "eps": w["eps"], "variant": VARIANT_NAMES[args.variant],
                    "storage": args.storage, "nrhs": nrhs, "tensor_cores": bool(args.tensor_cores) or args.storage == "bf16",
-                   "m2l": "fly" if info["m2l_fly"] else "stored",
+                   "m2l": {1: "fly", 2: "stored, formed on the device"}.get(info["m2l_fly"], "stored"),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "operators larger than L2 (no flush)",
                    "build_seconds": round(build_s, 2),
@@ -552,8 +553,10 @@ def main():
     ap.add_argument("--multi-rhs", default="bf16,tf32",
                     help="default workload only: also time the 64-RHS workload on the tensor "
                          "cores in these modes (comma list of bf16, tf32; '' for none)")
-    ap.add_argument("--m2l", default="stored", choices=["stored", "fly"],
-                    help="fp32 storage: evaluate M2L from the pivot coordinates")
+    ap.add_argument("--m2l", default="stored", choices=["stored", "fly", "device"],
+                    help="M2L blocks: stored (formed on the host), fly (fp32: evaluated "
+                         "from the pivot coordinates in each product), device (stored, "
+                         "formed on the device from the pivots)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="fp32 storage: RHS tiles of 16-64 columns on tcgen05 (tf32)")
     ap.add_argument("--variant", default="h2star", choices=list(VARIANT_NAMES))

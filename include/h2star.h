@@ -98,10 +98,14 @@ typedef struct {
     int    tensor_cores;   /* H2_F32 only: 1 = RHS tiles of 16-64 columns run on the
                               tensor cores in tf32 (10-bit significand multiplies,
                               fp32 accumulate); 0 (default) = fp32 CUDA-core FMA     */
-    int    m2l_mode;       /* H2_F32 only: 1 = the coupling blocks T_{X,Y} = G(t^{X,i},
-                              t^{Y,i}) (§3.6.4) are evaluated in each product from the
-                              pivot coordinates instead of being stored; 0 (default) =
-                              stored blocks                                          */
+    int    m2l_mode;       /* the coupling blocks T_{X,Y} = G(t^{X,i}, t^{Y,i}) (§3.6.4):
+                              0 (default) = stored, formed on the host and uploaded;
+                              1 (H2_F32 only) = evaluated in each product from the
+                              pivot coordinates, not stored; 2 = stored, formed on
+                              the device from the pivot coordinates (fp64 entries,
+                              each rounded once to the storage; the host never holds
+                              them, so host_only handles of this mode have no M2L
+                              values and batches refuse them)                        */
 } h2_build_opts;
 
 typedef struct h2_handle_s* h2_handle;
@@ -210,7 +214,9 @@ typedef struct {
     int     tc_blocks[3];          /* tensor-core products: persistent CTAs per launch for
                                       RHS tiles of 64 / 32 / 16 (0: no tensor cores)     */
     int     tc_occupancy[3];       /* the runtime's resident-CTA estimate per SM (report) */
-    int     m2l_fly;               /* 1: M2L evaluated from pivot coordinates           */
+    int     m2l_fly;               /* the build's m2l_mode: 0 stored (host-formed), 1 M2L
+                                      evaluated from pivot coordinates, 2 stored
+                                      (device-formed)                                    */
     int64_t m2l_entries;           /* entries of all T_{X,Y} (sum of rows x columns)     */
 } h2_stats;
 

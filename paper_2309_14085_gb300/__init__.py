@@ -23,6 +23,9 @@ KERNELS = {"log2d": 0, "invr": 1, "imq": 2, "matern12": 3}
 VARIANTS = {"h2star": 0, "h2plush": 1, "h2sqrt": 2, "h2star_t": 3, "h2sqrt_t": 4, "h2star_b": 5}
 STORAGE = {"f64": 0, "f32": 1, "df64": 2, "bf16": 3}
 NEAR = {None: 0, "fly": 1, "stored": 2}
+#: M2L coupling blocks: stored (formed on the host), evaluated in each product
+#: from the pivot coordinates (fp32 only), or stored and formed on the device
+M2L = {None: 0, "stored": 0, "fly": 1, "device": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
 EXPORTED = ("h2_build", "h2_convert", "h2_release_host", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
@@ -193,7 +196,7 @@ class H2Matrix:
         o.kparam = kparam or 0.0
         o.near_mode = NEAR[near]
         o.tensor_cores = int(tensor_cores)
-        o.m2l_mode = {None: 0, "stored": 0, "fly": 1}[m2l]
+        o.m2l_mode = M2L[m2l]
         h = ctypes.c_void_p()
         _check(lib().h2_build(P.ctypes.data, self.N, self.d, KERNELS[kernel], leaf_size, tol,
                               VARIANTS[variant], ctypes.byref(o), ctypes.byref(h)))

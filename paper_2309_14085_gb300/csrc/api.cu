@@ -434,6 +434,53 @@ int autotune(h2_handle h) {
     return H2_OK;
 }
 
+template <class A, int D>
+void launch_m2l_fill(const DevRowTasks& R, const double* px, const h2::Host& H, void* ops) {
+    using S = typename A::S;
+    const h2::Packed& P = H.packed;
+    const double c = H.kern.param, diag = H.kern.diag();
+    S* o = static_cast<S*>(ops);
+#define H2_FILL(KIND)                                                                          \
+    h2::k_m2l_fill<A, D, KIND><<<unsigned(R.n), 256>>>(R.n, R.dst, R.rows, R.kpad, R.aoff,      \
+                                                      R.seg_ptr, R.seg_off, R.seg_len,         \
+                                                      R.seg_col, px, P.vlen, P.v_base,          \
+                                                      P.u_base, c, diag, o)
+    switch (H.kern.kind) {
+        case 0: H2_FILL(0); break;
+        case 1: H2_FILL(1); break;
+        case 2: H2_FILL(2); break;
+        default: H2_FILL(3); break;
+    }
+#undef H2_FILL
+}
+
+// Stored M2L blocks formed on the device from the pivot coordinates (the host
+// keeps only the pivots): clear the region, upload the coordinates to a
+// temporary buffer, one fill launch over the M2L tasks, release the buffer.
+template <class A>
+int form_m2l(h2_handle h) {
+    using S = typename A::S;
+    const h2::Host& H = h->host;
+    const h2::Packed& P = H.packed;
+    if (P.pivot_x.size() != size_t(H.tree.d) * size_t(P.vlen))
+        return fail(H2_E_INVALID_ARG, "pivot coordinates missing for the device-formed M2L");
+    S* ops = static_cast<S*>(h->ops);
+    H2_CUDA(cudaMemset(ops + P.m2l_base, 0, size_t(P.m2l_len) * sizeof(S)));
+    void* px = nullptr;
+    cudaError_t e = cudaMalloc(&px, std::max<size_t>(P.pivot_x.size(), 1) * sizeof(double));
+    if (e != cudaSuccess) return fail(H2_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(px, P.pivot_x.data(), P.pivot_x.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && h->m2l.n > 0) {
+        if (H.tree.d == 2) launch_m2l_fill<A, 2>(h->m2l, static_cast<const double*>(px), H, ops);
+        else launch_m2l_fill<A, 3>(h->m2l, static_cast<const double*>(px), H, ops);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(px);
+    if (e != cudaSuccess) return fail(H2_E_CUDA, std::string("M2L fill: ") + cudaGetErrorString(e));
+    return H2_OK;
+}
+
 template <class A>
 int upload(h2_handle h) {
     using S = typename A::S;
@@ -442,9 +489,11 @@ int upload(h2_handle h) {
     const h2::Packed& P = H.packed;
     const h2::Tree& t = H.tree;
     h->vsize = sizeof(V);
+    // entries on the device: the host's ops, then (M2L formed on the device) its region
+    const size_t n_dev = H.m2l_dev ? size_t(P.m2l_base + P.m2l_len) : P.ops.size();
     {
         void* p = nullptr;
-        const size_t n = std::max<size_t>(P.ops.size(), 1);
+        const size_t n = std::max<size_t>(n_dev, 1);
         H2_TRY(dev_alloc(h, &p, n * sizeof(S)));
         if (std::is_same<S, double>::value) {
             if (!P.ops.empty())
@@ -460,7 +509,7 @@ int upload(h2_handle h) {
             }
         }
         h->ops = p;
-        h->ops_len = int64_t(P.ops.size());
+        h->ops_len = int64_t(n_dev);
     }
     if (!P.near_stored) {
         using T = typename std::conditional<std::is_same<A, h2::F32>::value, float, double>::type;
@@ -496,6 +545,7 @@ int upload(h2_handle h) {
     H2_TRY(dev_upload(h, &h->utoff, P.utoff));
     H2_TRY(upload_rows(h, h->p2m, P.p2m));
     H2_TRY(upload_rows(h, h->m2l, P.m2l));
+    if (H.m2l_dev && P.m2l_len > 0) H2_TRY(form_m2l<A>(h));
     H2_TRY(upload_rows(h, h->leaf, P.leaf));
     h->m2m.assign(t.kappa + 1, DevRowTasks());
     h->l2l.assign(t.kappa + 1, DevRowTasks());
@@ -828,7 +878,7 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(H2_E_INVALID_ARG, "tensor_cores must be 0 or 1");
     if (o.tensor_cores && o.storage != H2_F32)
         return fail(H2_E_INVALID_ARG, "tensor_cores applies to H2_F32 storage (H2_BF16 always uses them)");
-    if (o.m2l_mode < 0 || o.m2l_mode > 1) return fail(H2_E_INVALID_ARG, "unknown m2l_mode");
+    if (o.m2l_mode < 0 || o.m2l_mode > 2) return fail(H2_E_INVALID_ARG, "unknown m2l_mode");
     if (o.m2l_mode == 1 && o.storage != H2_F32)
         return fail(H2_E_UNSUPPORTED, "M2L on the fly is built for fp32 storage");
     if (o.storage == H2_BF16 && o.near_mode == 1)
@@ -869,7 +919,8 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     H.storage = o.storage;
     H.near_mode = o.near_mode;
     H.tensor_cores = o.tensor_cores;
-    H.m2l_fly = o.m2l_mode;
+    H.m2l_fly = o.m2l_mode == 1;
+    H.m2l_dev = o.m2l_mode == 2;
     H.eps_far = o.eps_far > 0 ? o.eps_far : tol;
     H.eps_ver = o.eps_ver > 0 ? o.eps_ver : tol;
     try {
@@ -1041,7 +1092,7 @@ int h2_info(h2_handle h, h2_stats* st) {
         st->tc_blocks[k] = h->tc_blocks[k];
         st->tc_occupancy[k] = h->tc_occupancy[k];
     }
-    st->m2l_fly = H.m2l_fly;
+    st->m2l_fly = H.m2l_fly ? 1 : H.m2l_dev ? 2 : 0;
     st->m2l_entries = 0;
     for (int64_t k = 0; k < P.m2l.size(); ++k) {
         int64_t cols = 0;
@@ -1636,6 +1687,8 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
         if (hs[i]->host.storage != storage) return fail(H2_E_INVALID_ARG, "handles differ in storage");
         if (storage == H2_BF16) return fail(H2_E_UNSUPPORTED, "batched products use fp64, fp32 or df64 storage");
         if (hs[i]->host.m2l_fly) return fail(H2_E_UNSUPPORTED, "batched products use stored M2L blocks");
+        if (hs[i]->host.m2l_dev && !hs[i]->on_device)
+            return fail(H2_E_UNSUPPORTED, "a host-only handle with device-formed M2L holds no M2L blocks");
         if (!hs[i]->host.packed.near_stored)
             return fail(H2_E_UNSUPPORTED, "batched products need the stored near field (near_mode 2)");
         if (hs[i]->host.variant == H2_PLUS_H_STAR)

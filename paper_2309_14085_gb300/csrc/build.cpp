@@ -504,8 +504,9 @@ std::string operators(const Host& H, Basis& B) {
                     solve_rows(B.tau[l + 1][Xc], B.Ut[l + 1][Xc]);
                 }
             // M2L: concatenated T_{X,Y} over Y in the list, r_X x sum r_Y (not
-            // stored when the product evaluates it from the pivots)
-            if (H.m2l_fly) continue;
+            // formed here when the product evaluates it from the pivots or the
+            // device forms it)
+            if (H.m2l_fly || H.m2l_dev) continue;
             const Csr& L = (*B.il)[l];
             int64_t kx = 0;
             for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) kx += B.rank(l, L.idx[e]);
@@ -715,8 +716,11 @@ void pack(Host& H) {
                 P.m2m[l].close();
             }
     }
-    // M2L: one block row per target, rows padded with zeros to a multiple of 4
+    // M2L: one block row per target, rows padded with zeros to a multiple of 4;
+    // blocks formed on the device get offsets in a region of their own, moved
+    // past the end of ops once every other block is placed
     P.m2l = RowTasks();
+    int64_t m2l_total = 0;
     for (int b = 0; b < P.nb; ++b) {
         const Basis& B = H.bases[b];
         for (int l = B.lmin; l <= K; ++l) {
@@ -729,6 +733,9 @@ void pack(Host& H) {
                 const int64_t kp = pad4(kx);
                 if (H.m2l_fly) {
                     P.m2l.add(P.u_base + P.voff[slot(b, l, X)], r, int32_t(kp), 0);
+                } else if (H.m2l_dev) {
+                    P.m2l.add(P.u_base + P.voff[slot(b, l, X)], r, int32_t(kp), m2l_total);
+                    m2l_total += int64_t(r) * kp;          // r * kp is a multiple of 4
                 } else {
                     const int64_t o = place(int64_t(r) * kp);
                     P.m2l.add(P.u_base + P.voff[slot(b, l, X)], r, int32_t(kp), o);
@@ -742,8 +749,8 @@ void pack(Host& H) {
             }
         }
     }
-    if (H.m2l_fly) {
-        P.m2l.entries = 0;                              // nothing stored
+    if (H.m2l_fly || H.m2l_dev) {
+        if (H.m2l_fly) P.m2l.entries = 0;               // nothing stored
         // pivot coordinates in the coefficient layout: slot (b, l, X) holds the
         // incoming pivots t^{X,i} of that cluster, in pivot order
         P.pivot_x.assign(size_t(d) * size_t(P.vlen), 0.0);
@@ -792,6 +799,10 @@ void pack(Host& H) {
         for (int l = 0; l <= K; ++l) P.lr_level_ptr[l + 1] += P.lr_level_ptr[l];
     }
     total = (total + 3) / 4 * 4;
+    P.m2l_base = total;
+    P.m2l_len = H.m2l_dev ? m2l_total : 0;
+    if (H.m2l_dev)
+        for (int64_t& a : P.m2l.aoff) a += total;
     std::vector<double>().swap(P.ops);
     P.ops.assign(size_t(total), 0.0);     // zero: padding and alignment gaps
 #pragma omp parallel for schedule(dynamic, 16)

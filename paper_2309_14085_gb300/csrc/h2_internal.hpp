@@ -114,8 +114,12 @@ struct RowTasks {
 // is [ q (N) | v (vlen) | u (vlen) | phi (N) ].
 struct Packed {
     int nb = 0;                       // nested bases (1 or 2)
-    std::vector<double> pivot_x;      // M2L on the fly: d x vlen pivot coordinates, in the
-                                      // v / u coefficient layout (coordinate-major)
+    std::vector<double> pivot_x;      // M2L on the fly or formed on the device: d x vlen
+                                      // pivot coordinates, in the v / u coefficient layout
+                                      // (coordinate-major)
+    int64_t m2l_base = 0;             // M2L formed on the device: its blocks occupy entries
+    int64_t m2l_len = 0;              // [m2l_base, m2l_base + m2l_len) of the device array,
+                                      // past the end of ops (not held on the host)
     int near_stored = 0;              // 1: near field stored as leaf block rows
     int64_t box_total = 0;            // boxes over levels 0..kappa
     std::vector<int64_t> box_base;    // first box id of each level
@@ -148,6 +152,7 @@ struct Host {
     int near_mode = 0;               // 0 default, 1 on the fly, 2 stored
     int tensor_cores = 0;            // fp32 storage: multi-RHS tiles on tcgen05 (tf32)
     int m2l_fly = 0;                 // 1: M2L from pivot coordinates, T not stored
+    int m2l_dev = 0;                 // 1: T stored, formed on the device from the pivots
     double eps_far = 0, eps_ver = 0;
     Tree tree;
     Lists lists;

@@ -741,4 +741,85 @@ __global__ void k_lr_ut(int64_t g0, int64_t ngroup, const int64_t* __restrict__ 
     phi[(x0[bfirst] + i) * nrhs + col] += acc;
 }
 
+// ---- M2L blocks formed on the device ------------------------------------
+// G(r) from r^2 in fp64 with every operation rounded on its own (no fused
+// multiply-add), the same operations as the host construction: r = sqrt(r^2);
+// log r, 1 / r, 1 / sqrt(1 + (r / c)^2), exp(-r).
+template <int KIND>
+__device__ __forceinline__ double fill_kernel(double r2, double c, double diag) {
+    if (r2 == 0.0) return diag;
+    const double r = __dsqrt_rn(r2);
+    if constexpr (KIND == 0) return log(r);
+    else if constexpr (KIND == 1) return __ddiv_rn(1.0, r);
+    else if constexpr (KIND == 2) {
+        const double s = __ddiv_rn(r, c);
+        return __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(s, s))));
+    } else return exp(-r);
+}
+
+// fp64 -> stored entry, rounded once (bf16: round-to-nearest-even of the
+// float's upper 16 bits; double-float: hi = fl32(a), lo = fl32(a - hi))
+template <class A> struct StoreAs;
+template <> struct StoreAs<F64> {
+    __device__ static double of(double a) { return a; }
+};
+template <> struct StoreAs<F32> {
+    __device__ static float of(double a) { return __double2float_rn(a); }
+};
+template <> struct StoreAs<BF16> {
+    __device__ static __nv_bfloat16 of(double a) {
+        const uint32_t u = __float_as_uint(__double2float_rn(a));
+        const uint16_t b = ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu))
+                               ? uint16_t(0x7FC0)
+                               : uint16_t((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+        return __ushort_as_bfloat16(b);
+    }
+};
+template <> struct StoreAs<DF> {
+    __device__ static float2 of(double a) {
+        const float hi = __double2float_rn(a);
+        return make_float2(hi, __double2float_rn(__dsub_rn(a, double(hi))));
+    }
+};
+
+// Stored coupling blocks T_{X,Y} = G(t^{X,i}, t^{Y,i}) (§3.6.4) written by the
+// device from the pivot coordinates: one CTA per M2L task (target X) fills its
+// block row, rows x kpad row-major at ops + aoff; column k of segment e is the
+// source pivot whose coefficient sits at seg_off[e] + (k - seg_col[e]), row r
+// the target pivot of coefficient dst + r.  px[k * vlen + o] is coordinate k
+// of the pivot of v / u offset o.  Threads run along the columns of one row
+// segment, so the writes are contiguous; padding columns are not written (the
+// caller clears the region first).
+template <class A, int D, int KIND>
+__global__ void __launch_bounds__(256) k_m2l_fill(
+    int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
+    const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
+    const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
+    const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
+    const double* __restrict__ px, int64_t vlen, int64_t v_base, int64_t u_base, double param,
+    double diag, typename A::S* __restrict__ ops) {
+    const int64_t t = blockIdx.x;
+    if (t >= ntask) return;
+    const int nr = rows[t];
+    const int64_t kp = kpad[t];
+    const int64_t d0 = dst[t] - u_base;
+    typename A::S* Am = ops + aoff[t];
+    for (int64_t e = seg_ptr[t]; e < seg_ptr[t + 1]; ++e) {
+        const int len = seg_len[e];
+        const int64_t col = seg_col[e];
+        const int64_t s0 = seg_off[e] - v_base;
+        const int64_t n = int64_t(nr) * len;
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+            const int r = int(j / len), c = int(j - int64_t(r) * len);
+            double r2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const double dx = __dsub_rn(px[k * vlen + d0 + r], px[k * vlen + s0 + c]);
+                r2 = __dadd_rn(r2, __dmul_rn(dx, dx));
+            }
+            Am[int64_t(r) * kp + col + c] = StoreAs<A>::of(fill_kernel<KIND>(r2, param, diag));
+        }
+    }
+}
+
 }  // namespace h2

@@ -137,6 +137,39 @@ def test_m2l_on_the_fly_stores_no_coupling_blocks():
     assert F["ranks"] == S["ranks"]
 
 
+def test_device_formed_m2l_keeps_the_construction_and_the_accounting():
+    """m2l_mode 2 changes where the coupling blocks are formed, not what is
+    built: the same pivots and the same stored M2L entries as mode 0."""
+    P = inputs.points(3000, 3, 6)
+    kw = dict(leaf_size=32, tol=1e-6, host_only=True)
+    o = pkg.BuildOpts()
+    o.host_only, o.m2l_mode = 1, 3
+    h = ctypes.c_void_p()
+    Pc = np.ascontiguousarray(P)
+    assert pkg.lib().h2_build(Pc.ctypes.data, 3000, 3, 1, 32, 1e-6, 0, ctypes.byref(o),
+                              ctypes.byref(h)) == -1
+    for variant, storage in [("h2star", "f64"), ("h2sqrt", "f32"), ("h2plush", "f64"),
+                             ("h2star_t", "bf16")]:
+        S = H2Matrix(P, "invr", variant=variant, storage=storage, **kw)
+        D = H2Matrix(P, "invr", variant=variant, storage=storage, m2l="device", **kw)
+        a, b = S.info(), D.info()
+        assert a["m2l_fly"] == 0 and b["m2l_fly"] == 2
+        for k in ("bytes_m2l", "m2l_pairs", "m2l_src_coeffs", "m2l_dst_coeffs", "vlen",
+                  "bytes_basis", "bytes_transfer"):
+            assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+        for basis in range(a["nbases"]):
+            for l in range(1, a["kappa"] + 1):
+                for X in (0, 5):
+                    assert all(np.array_equal(u, v) for u, v in
+                               zip(S.pivots(basis, l, X), D.pivots(basis, l, X)))
+    # a host-only handle of this mode holds no M2L values: batches refuse it
+    D = H2Matrix(P, "invr", near="stored", m2l="device", **kw)
+    hs = (ctypes.c_void_p * 1)(D._h.value)
+    out = ctypes.c_void_p()
+    assert pkg.lib().h2_batch_create(hs, 1, None, ctypes.byref(out)) == -5
+    assert b"host-only" in pkg.lib().h2_last_error()
+
+
 def test_near_field_storage_accounting():
     P = inputs.points(4096, 2, 1001)
     S = H2Matrix(P, "log2d", leaf_size=64, tol=1e-6, host_only=True).info()
