@@ -94,6 +94,15 @@ def poisson_arrivals(count, rate, ngeom, seed=4999):
     return t - t[0], g
 
 
+def uniform_grid(n, d):
+    """Collocation points of the integral-equation experiments: the centres
+    -1 + (2 i + 1) / n, i < n, of the n^d cells of a uniform grid on [-1, 1]^d
+    (cell measure (2 / n)^d), in lexicographic order."""
+    x = -1.0 + (2.0 * np.arange(n) + 1.0) / n
+    g = np.meshgrid(*([x] * d), indexing="ij")
+    return np.stack([a.ravel() for a in g], axis=1)
+
+
 def chebyshev_grid(n, d):
     """The n^d tensor grid of Chebyshev points cos(pi (2i + 1) / (2n)), i < n, in
     [-1, 1]^d: the non-uniform point sets of the paper's Chebyshev experiments

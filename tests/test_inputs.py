@@ -50,3 +50,18 @@ def test_chebyshev_grid():
     assert g.shape == (25, 2)
     assert np.allclose(np.unique(g[:, 0]), np.sort(x))
     assert np.array_equal(g[:5, 0], np.full(5, x[0])) and np.allclose(g[:5, 1], x)
+
+
+def test_uniform_grid():
+    for n, d in [(64, 2), (16, 3)]:
+        g = inputs.uniform_grid(n, d)
+        assert g.shape == (n ** d, d)
+        h = 2.0 / n
+        # cell centres: one per cell, half a cell from the faces, spacing h
+        assert np.allclose(g.min(0), -1 + h / 2) and np.allclose(g.max(0), 1 - h / 2)
+        assert len(np.unique(np.round(g / h, 6), axis=0)) == n ** d
+        assert np.allclose(np.diff(np.unique(g[:, 0])), h)
+        # with n a power of two no centre lies on a box boundary of any level
+        for level in range(1, int(np.log2(n)) + 1):
+            t = (g + 1.0) * 2 ** level / 2.0
+            assert np.all(np.abs(t - np.round(t)) > 1e-9)
