@@ -386,6 +386,29 @@ def test_gmres_with_compressed_operator_re_sol():
     assert np.linalg.norm(x - q) / np.linalg.norm(q) < 1e-8
 
 
+@pytest.mark.parametrize("kind,d,n,eps,rtol", [("log2d", 2, 32, 1e-10, 1e-12),
+                                              ("invr", 3, 8, 1e-6, 1e-10)])
+def test_integral_equation_re_sol_on_the_collocation_grid(kind, d, n, eps, rtol):
+    """The second-kind integral equations of §6 on the uniform collocation
+    grid, (I + s K) sigma = f with s = -h^2/(2 pi) (2D, -(1/2pi) log r) or
+    h^3/(4 pi) (3D, 1/(4 pi r)): with b = K q the exact solution is q, and the
+    compressed solve stays within eps + 10 eps_GMRES of it."""
+    P = inputs.uniform_grid(n, d)
+    N = len(P)
+    h = 2.0 / n
+    s = -h ** 2 / (2 * math.pi) if d == 2 else h ** 3 / (4 * math.pi)
+    q = inputs.rhs(N, 1, 811)
+    b = q + s * dense.product(kind, P, q)
+    assert np.linalg.norm(b - q) < 0.1 * np.linalg.norm(q)
+    H = h2.H2(P, kind, n_max=16 if d == 2 else 8, eps=eps)
+    x, hist, it = gmres.gmres(lambda v: v + s * H.matvec(v), b, rtol=rtol, maxit=200)
+    assert hist[-1] < rtol
+    assert np.linalg.norm(x - q) / np.linalg.norm(q) <= eps + 10 * rtol
+    # the same system solved densely returns q to rounding
+    xd = gmres.dense_solve(np.eye(N) + s * dense.matrix(kind, P), b)
+    assert np.linalg.norm(xd - q) <= 1e-13 * np.linalg.norm(q)
+
+
 def test_b2t_over_the_weak_admissibility_loses_accuracy_and_t2b_does_not():
     """§4's central observation, reproduced at a small size: with far-field and
     vertex-sharing clusters both admissible, B2T NCA over the whole list leaves
