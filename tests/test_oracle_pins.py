@@ -11,7 +11,6 @@ import os
 
 import numpy as np
 import pytest
-import scipy.linalg
 
 from oracle import aca, dense, gmres, h2, kernels, tree
 from paper_2309_14085_gb300 import inputs
