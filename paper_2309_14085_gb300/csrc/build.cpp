@@ -289,10 +289,50 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         // one pass over the previous crosses: v_l . v for the norm update and,
         // when the next row is known, its residual (same order of operations
         // as computing them separately)
+        // Four crosses per sweep over j: each v_l . v is still summed in j
+        // order and each rn[j] still takes its subtractions in l order, so
+        // the results are those of one cross at a time, but four independent
+        // addition chains hide the latency of the sequential sums.
         pv.assign(us.size(), 0.0);
         if (fuse)
             for (int64_t j = 0; j < nJ; ++j) rn[j] = entry(ib, j);
-        for (size_t l = 0; l < us.size(); ++l) {
+        const size_t np = us.size();
+        size_t l = 0;
+        for (; l + 4 <= np; l += 4) {
+            const double *v0 = vs[l].data(), *v1 = vs[l + 1].data(), *v2 = vs[l + 2].data(),
+                         *v3 = vs[l + 3].data();
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            if (fuse) {
+                const double a0 = us[l][ib], a1 = us[l + 1][ib], a2 = us[l + 2][ib],
+                             a3 = us[l + 3][ib];
+                for (int64_t j = 0; j < nJ; ++j) {
+                    double x = rn[j];
+                    x = x - a0 * v0[j];
+                    x = x - a1 * v1[j];
+                    x = x - a2 * v2[j];
+                    x = x - a3 * v3[j];
+                    rn[j] = x;
+                    const double vj = v[j];
+                    s0 += v0[j] * vj;
+                    s1 += v1[j] * vj;
+                    s2 += v2[j] * vj;
+                    s3 += v3[j] * vj;
+                }
+            } else {
+                for (int64_t j = 0; j < nJ; ++j) {
+                    const double vj = v[j];
+                    s0 += v0[j] * vj;
+                    s1 += v1[j] * vj;
+                    s2 += v2[j] * vj;
+                    s3 += v3[j] * vj;
+                }
+            }
+            pv[l] = s0;
+            pv[l + 1] = s1;
+            pv[l + 2] = s2;
+            pv[l + 3] = s3;
+        }
+        for (; l < np; ++l) {
             const double* vl = vs[l].data();
             double s = 0.0;
             if (fuse) {
@@ -381,6 +421,15 @@ void lu_solve(const std::vector<double>& A, int n, const std::vector<int>& piv, 
 
 // ---------------------------------------------------------------------------
 // Pivot selection
+
+// with H2_VERBOSE set: the time of one level of a pivot sweep, on stderr
+void level_time(const char* what, int l, std::chrono::steady_clock::time_point t0) {
+    static const bool verbose = std::getenv("H2_VERBOSE") != nullptr;
+    if (!verbose) return;
+    std::fprintf(stderr, "[h2 build]   %s level %2d %8.3f s\n", what, l,
+                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+}
+
 void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps, int lmin = 2) {
     const Tree& t = H.tree;
     const int K = t.kappa, d = t.d;
@@ -391,6 +440,7 @@ void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps, int lm
     for (int l = 0; l <= K; ++l) { B.tau[l].resize(t.nboxes(l)); B.sig[l].resize(t.nboxes(l)); }
     for (int l = K; l >= lmin; --l) {
         const int64_t n = t.nboxes(l);
+        const auto tl = std::chrono::steady_clock::now();
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t X = 0; X < n; ++X) {
             std::vector<int64_t> I, J;
@@ -421,6 +471,7 @@ void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps, int lm
             for (int a : R.rows) tau.push_back(I[a]);
             for (int a : R.cols) sig.push_back(J[a]);
         }
+        level_time("b2t", l, tl);
     }
 }
 
@@ -434,6 +485,7 @@ void t2b(const Host& H, Basis& B, const std::vector<Csr>& il, double eps) {
     for (int l = 0; l <= K; ++l) { B.tau[l].resize(t.nboxes(l)); B.sig[l].resize(t.nboxes(l)); }
     for (int l = 1; l <= K; ++l) {
         const int64_t n = t.nboxes(l);
+        const auto tl = std::chrono::steady_clock::now();
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t X = 0; X < n; ++X) {
             std::vector<int64_t> I, J;
@@ -452,6 +504,7 @@ void t2b(const Host& H, Basis& B, const std::vector<Csr>& il, double eps) {
             for (int a : R.rows) B.tau[l][X].push_back(I[a]);
             for (int a : R.cols) B.sig[l][X].push_back(J[a]);
         }
+        level_time("t2b", l, tl);
     }
 }
 
