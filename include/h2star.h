@@ -159,6 +159,27 @@ int h2_release_host(h2_handle h);
 int h2_convert(h2_handle src, int storage, h2_handle* out);
 
 /*
+ * h2_save / h2_load -- checkpoint of a constructed representation (the paper
+ * has no counterpart; construction dominates its run times).  h2_save writes
+ * the handle's whole host state -- tree, interaction lists, pivots, operators
+ * and the packed device layout, with its kernel, variant, storage and modes --
+ * to the file `path` (host; native little-endian, 64-bit sizes).  h2_load reads
+ * it into a new handle: host-only if host_only = 1, else uploaded to the
+ * current CUDA device in the saved storage, with the same products as the
+ * saved handle's; M2L blocks formed on the device (m2l_mode 2) are formed again
+ * there.  A loaded file is bounds-checked field by field (every length against
+ * the bytes left) and then index by index against the buffers the device
+ * kernels address, so a truncated or corrupted file is an error, never an
+ * out-of-range access.
+ * Errors: H2_E_INVALID_ARG (NULL argument, file not readable or writable, not
+ * a checkpoint, truncated or inconsistent), H2_E_UNSUPPORTED (h2_save of a
+ * handle whose host operators were released), H2_E_OOM, H2_E_NO_DEVICE,
+ * H2_E_CUDA.
+ */
+int h2_save(h2_handle h, const char* path);
+int h2_load(const char* path, int host_only, h2_handle* out);
+
+/*
  * h2_matvec -- Y = K~ X for nrhs right-hand sides (§5.1.2 / §5.2.2 / App. A.2,
  * App. B.2 and App. C.2 for the T2B-only variants).
  *

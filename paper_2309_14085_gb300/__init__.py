@@ -31,7 +31,7 @@ EXPORTED = ("h2_build", "h2_convert", "h2_release_host", "h2_matvec", "h2_gmres"
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
             "h2_batch_matvec", "h2_batch_info", "h2_batch_destroy", "h2_server_create",
             "h2_server_submit", "h2_server_wait", "h2_server_stats_get", "h2_server_destroy",
-            "h2_inject_wait_expiry")
+            "h2_inject_wait_expiry", "h2_save", "h2_load")
 
 
 class BuildOpts(ctypes.Structure):
@@ -140,6 +140,8 @@ def lib():
         L.h2_convert.argtypes = [c_vp, c_int, ctypes.POINTER(c_vp)]
         L.h2_release_host.argtypes = [c_vp]
         L.h2_inject_wait_expiry.argtypes = [c_vp, c_i64, c_vp]
+        L.h2_save.argtypes = [c_vp, ctypes.c_char_p]
+        L.h2_load.argtypes = [ctypes.c_char_p, c_int, ctypes.POINTER(c_vp)]
         L.h2_server_create.argtypes = [c_vp, c_vp, c_int, ctypes.POINTER(ServerOpts),
                                        ctypes.POINTER(c_vp)]
         L.h2_server_submit.argtypes = [c_vp, c_int, c_dbl, c_dbl, c_vp, c_dbl, c_int,
@@ -210,6 +212,26 @@ class H2Matrix:
         m = H2Matrix.__new__(H2Matrix)
         m.N, m.d, m.kernel, m.variant, m.storage = self.N, self.d, self.kernel, self.variant, storage
         m._h = h
+        return m
+
+    def save(self, path):
+        """Write the whole constructed representation to `path` (h2_save)."""
+        _check(lib().h2_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path, host_only=False):
+        """A matrix read from a file written by save(): host-only, or uploaded to
+        the current CUDA device in the saved storage (h2_load)."""
+        h = ctypes.c_void_p()
+        _check(lib().h2_load(os.fsencode(path), int(host_only), ctypes.byref(h)))
+        m = cls.__new__(cls)
+        m._h = h
+        st = m.info()
+        inv = lambda table, v: next(k for k, x in table.items() if x == v)
+        m.N, m.d = st["N"], st["d"]
+        m.kernel = inv(KERNELS, st["kernel"])
+        m.variant = inv(VARIANTS, st["variant"])
+        m.storage = inv(STORAGE, st["storage"])
         return m
 
     def release_host(self):

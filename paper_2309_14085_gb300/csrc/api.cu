@@ -986,6 +986,7 @@ int h2_convert(h2_handle src, int storage, h2_handle* out) {
     } catch (const std::bad_alloc&) {
         return fail(H2_E_OOM, "host allocation failed");
     }
+    h2::relink_lists(h->host);           // the copy's bases still point at src's lists
     h->host.storage = storage;
     h->host.near_mode = stored ? 2 : 1;
     if (storage != H2_F32) h->host.tensor_cores = 0;
@@ -996,6 +997,53 @@ int h2_convert(h2_handle src, int storage, h2_handle* out) {
         return rc;
     }
     h->on_device = true;
+    *out = h.release();
+    return H2_OK;
+}
+
+int h2_save(h2_handle h, const char* path) {
+    g_err.clear();
+    if (!h || !path) return fail(H2_E_INVALID_ARG, "NULL argument");
+    if (h->host.packed.ops.empty() && h->on_device && h->ops_len > h->host.packed.m2l_len)
+        return fail(H2_E_UNSUPPORTED, "the handle's host operators were released (h2_release_host)");
+    std::string e;
+    try {
+        e = h2::save_host(h->host, path);
+    } catch (const std::bad_alloc&) {
+        return fail(H2_E_OOM, "host allocation failed");
+    }
+    if (!e.empty()) return fail(H2_E_INVALID_ARG, e);
+    return H2_OK;
+}
+
+int h2_load(const char* path, int host_only, h2_handle* out) {
+    g_err.clear();
+    if (!out) return fail(H2_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!path) return fail(H2_E_INVALID_ARG, "path is NULL");
+    if (host_only != 0 && host_only != 1) return fail(H2_E_INVALID_ARG, "host_only must be 0 or 1");
+    std::unique_ptr<h2_handle_s> h;
+    try {
+        h.reset(new h2_handle_s());
+        std::string e = h2::load_host(h->host, path);
+        if (!e.empty()) return fail(H2_E_INVALID_ARG, e);
+    } catch (const std::bad_alloc&) {
+        return fail(H2_E_OOM, "host allocation failed while loading");
+    }
+    if (!host_only) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+            cudaGetLastError();
+            return fail(H2_E_NO_DEVICE, "no CUDA device");
+        }
+        H2_CUDA(cudaGetDevice(&h->device));
+        int rc = upload_any(h.get());
+        if (rc != H2_OK) {
+            h2_destroy(h.release());
+            return rc;
+        }
+        h->on_device = true;
+    }
     *out = h.release();
     return H2_OK;
 }

@@ -938,14 +938,17 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
     if (H.variant == 0 || H.variant == 1) {
         H.bases.emplace_back();
         b2t(H, H.bases.back(), H.lists.far, H.eps_far);
+        H.bases.back().il_kind = 0;
     }
     if (H.variant == 0) {
         H.bases.emplace_back();
         t2b(H, H.bases.back(), H.lists.ver, H.eps_ver);
+        H.bases.back().il_kind = 1;
     }
     if (H.variant == 2) {
         H.bases.emplace_back();
         b2t(H, H.bases.back(), H.lists.sqrtd, H.eps_far);
+        H.bases.back().il_kind = 2;
     }
     if (H.variant == 3 || H.variant == 5) {
         // IL_* = IL_far u IL_ver per box
@@ -970,11 +973,13 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
             t2b(H, H.bases.back(), H.lists.star, H.eps_far);
         else                  // §4.1: B2T NCA over the whole IL_*, levels kappa .. 1
             b2t(H, H.bases.back(), H.lists.star, H.eps_far, 1);
+        H.bases.back().il_kind = 3;
     }
     if (H.variant == 4) {
         // H2_sqrt(d)(t) (App. B): one basis, T2B NCA over the strong-admissibility lists
         H.bases.emplace_back();
         t2b(H, H.bases.back(), H.lists.sqrtd, H.eps_far);
+        H.bases.back().il_kind = 2;
     }
     tick("pivots");
     for (Basis& B : H.bases) {

@@ -67,6 +67,7 @@ struct Lists {
 // pivots are t^{X,o} = s^{X,i}, s^{X,o} = t^{X,i} and V = U.
 struct Basis {
     int lmin = 0;
+    int il_kind = 0;                                          // il: 0 far, 1 ver, 2 sqrtd, 3 star
     const std::vector<Csr>* il = nullptr;                    // interaction lists used
     std::vector<std::vector<std::vector<int64_t>>> tau, sig;  // [l][X] t^{X,i}, s^{X,i}
     std::vector<std::vector<double>> U;                       // [leaf] m x r row-major (L2P)
@@ -168,5 +169,13 @@ struct Host {
 std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf_size,
                        int kappa_forced, const double* domain_lo, double domain_side,
                        int threads);
+
+// Point every basis's list pointer into H's own lists (after a copy or a load).
+void relink_lists(Host& H);
+
+// Checkpoint of the whole host state (serialize.cpp).  Return "" on success or
+// an error message; load_host checks every offset the device kernels use.
+std::string save_host(const Host& H, const char* path);
+std::string load_host(Host& H, const char* path);
 
 }  // namespace h2

@@ -1,0 +1,105 @@
+"""Checkpoints of a constructed representation (h2_save / h2_load), on the
+CPU with host-only handles: a saved and reloaded construction is the same one
+(statistics, tree order, every pivot, and the file written again byte for
+byte), and truncated or corrupted files are rejected with an error code."""
+
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import paper_2309_14085_gb300 as pkg
+from paper_2309_14085_gb300 import H2Error, H2Matrix, inputs
+
+CASES = [
+    dict(kernel="invr", d=3, N=3000, variant="h2star", storage="f64"),
+    dict(kernel="log2d", d=2, N=4096, variant="h2plush", storage="f32"),
+    dict(kernel="imq", d=2, N=2500, variant="h2sqrt", storage="df64", kparam=0.5),
+    dict(kernel="log2d", d=2, N=3000, variant="h2star_t", storage="bf16"),
+    dict(kernel="invr", d=3, N=3000, variant="h2sqrt_t", storage="f32", m2l="fly"),
+    dict(kernel="matern12", d=3, N=2000, variant="h2star_b", storage="f64", m2l="device"),
+]
+
+
+def _build(c):
+    c = dict(c)
+    P = inputs.points(c.pop("N"), c.pop("d"), 91)
+    return H2Matrix(P, c.pop("kernel"), leaf_size=32, tol=1e-6, host_only=True, **c)
+
+
+def _pivots(A):
+    i = A.info()
+    out = []
+    for b in range(i["nbases"]):
+        for l in range(i["kappa"] + 1):
+            for X in range(1 << (i["d"] * l)):
+                out.append(A.pivots(b, l, X))
+    return out
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c['variant']}-{c['storage']}" for c in CASES])
+def test_saved_and_loaded_construction_is_the_same(tmp_path, case):
+    A = _build(case)
+    f1, f2 = str(tmp_path / "a.h2"), str(tmp_path / "b.h2")
+    A.save(f1)
+    B = H2Matrix.load(f1, host_only=True)
+    assert (B.N, B.d, B.kernel, B.variant, B.storage) == (A.N, A.d, case["kernel"],
+                                                          case["variant"], case["storage"])
+    ia, ib = A.info(), B.info()
+    assert ia == ib
+    assert np.array_equal(A.tree_order(), B.tree_order())
+    for (ta, sa), (tb, sb) in zip(_pivots(A), _pivots(B)):
+        assert np.array_equal(ta, tb) and np.array_equal(sa, sb)
+    B.save(f2)
+    assert open(f1, "rb").read() == open(f2, "rb").read()
+
+
+def test_truncated_and_corrupted_files_are_rejected(tmp_path):
+    A = _build(CASES[0])
+    path = str(tmp_path / "a.h2")
+    A.save(path)
+    data = open(path, "rb").read()
+    bad = str(tmp_path / "bad.h2")
+
+    def load(blob):
+        with open(bad, "wb") as f:
+            f.write(blob)
+        return H2Matrix.load(bad, host_only=True)
+
+    for cut in (0, 7, 8, 100, len(data) // 2, len(data) - 1):
+        with pytest.raises(H2Error) as e:
+            load(data[:cut])
+        assert e.value.code == -1
+    for blob in (b"X" + data[1:], data + b"\0"):
+        with pytest.raises(H2Error) as e:
+            load(blob)
+        assert e.value.code == -1
+    # single-byte corruptions: either rejected or a consistent state
+    rng = np.random.default_rng(93)
+    loaded = rejected = 0
+    for pos in rng.integers(8, len(data), size=60):
+        blob = bytearray(data)
+        blob[int(pos)] ^= 0xFF
+        try:
+            B = load(bytes(blob))
+        except H2Error as err:
+            assert err.code in (-1, -2)
+            rejected += 1
+        else:
+            B.info()
+            loaded += 1
+    assert rejected > 0 and loaded + rejected == 60
+    with pytest.raises(H2Error) as e:
+        H2Matrix.load(str(tmp_path / "missing.h2"), host_only=True)
+    assert e.value.code == -1
+
+
+def test_abi_arguments(tmp_path):
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    assert L.h2_load(None, 1, ctypes.byref(h)) == -1
+    assert L.h2_load(b"x", 2, ctypes.byref(h)) == -1
+    assert L.h2_save(None, b"x") == -1
+    A = _build(CASES[0])
+    assert L.h2_save(A._h, os.fsencode(str(tmp_path / "no-such-dir" / "x.h2"))) == -1
