@@ -288,11 +288,11 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         const bool fuse = bi > 0.0;
         // one pass over the previous crosses: v_l . v for the norm update and,
         // when the next row is known, its residual (same order of operations
-        // as computing them separately)
-        // Four crosses per sweep over j: each v_l . v is still summed in j
-        // order and each rn[j] still takes its subtractions in l order, so
-        // the results are those of one cross at a time, but four independent
-        // addition chains hide the latency of the sequential sums.
+        // as computing them separately).  Four crosses share a sweep over j:
+        // each v_l . v is still summed in j order and each rn[j] still takes
+        // its subtractions in l order, so the results are those of one cross
+        // at a time, while four independent addition chains hide the latency
+        // of the sequential sums.
         pv.assign(us.size(), 0.0);
         if (fuse)
             for (int64_t j = 0; j < nJ; ++j) rn[j] = entry(ib, j);
