@@ -120,15 +120,20 @@ typedef struct h2_handle_s* h2_handle;
  *              leaf_size * 2^(d kappa) >= N unless opts->kappa forces it.
  *   tol        ACA / NCA tolerance eps of §3.6 (> 0, < 1), used for eps_far
  *              and eps_ver unless opts sets them (§6 uses eps = eps_far = eps_ver).
- *   variant    H2_STAR_BT, H2_PLUS_H_STAR or H2_SQRTD_B.
+ *   variant    H2_STAR_BT, H2_PLUS_H_STAR, H2_SQRTD_B, H2_STAR_T, H2_SQRTD_T or
+ *              H2_STAR_B.
  *   opts       NULL or build options (above).
  *   out        receives the handle (owns all host and device memory).
  *
  * The tree (§3.1), the interaction lists (§3.5 / §3.3), the pivots (B2T NCA
  * Algorithm 1, T2B NCA §5.1.1, ACA §3.6) and the operators (§3.6.4) are built
  * on the host with OpenMP; the operators are then packed per level and copied
- * to the current CUDA device (synchronously, on the legacy default stream).
- * Errors: H2_E_INVALID_ARG, H2_E_OOM, H2_E_CUDA, H2_E_NO_DEVICE.
+ * to the current CUDA device (synchronously, on the legacy default stream),
+ * where m2l_mode 2 forms the coupling blocks instead of copying them.
+ * Errors: H2_E_INVALID_ARG, H2_E_UNSUPPORTED (an option this storage or
+ * variant does not implement, e.g. m2l_mode 1 without H2_F32, on-the-fly near
+ * field in H2_DF64 / H2_BF16, (H2+H)* in H2_DF64 / H2_BF16), H2_E_OOM,
+ * H2_E_CUDA, H2_E_NO_DEVICE.
  */
 int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size,
              double tol, int variant, const h2_build_opts* opts, h2_handle* out);
