@@ -228,6 +228,27 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         for (int k = 0; k < d; ++k) { const double q = xI[i * d + k] - xJ[j * d + k]; s = s + q * q; }
         return G(s);
     };
+    // a whole row K(x_i, x_J): for 1/r and the IMQ the same operations as
+    // entry() in a loop without calls or branches, which the compiler turns
+    // into vector square roots and divisions (IEEE, so the values are equal)
+    auto entry_row = [&](int64_t i, double* out) {
+        const double* xi = xI.data() + i * d;
+        if (G.kind == 1 || G.kind == 2) {
+            const double diag = G.diag(), c = G.param;
+            const bool imq = G.kind == 2;
+            for (int64_t j = 0; j < nJ; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < d; ++k) { const double q = xi[k] - xJ[j * d + k]; s = s + q * q; }
+                const double r = std::sqrt(s);
+                double g;
+                if (imq) { const double t = r / c; g = 1.0 / std::sqrt(1.0 + t * t); }
+                else g = 1.0 / r;
+                out[j] = s == 0.0 ? diag : g;
+            }
+        } else {
+            for (int64_t j = 0; j < nJ; ++j) out[j] = entry(i, j);
+        }
+    };
     std::vector<std::vector<double>>& us = out.us;
     std::vector<std::vector<double>>& vs = out.vs;
     std::vector<char> row_used(nI, 0), col_used(nJ, 0);
@@ -242,7 +263,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
     };
     // residual row of row position `ir` against every accepted cross, l in order
     auto fresh_row = [&](int64_t ir, std::vector<double>& out_r) {
-        for (int64_t j = 0; j < nJ; ++j) out_r[j] = entry(ir, j);
+        entry_row(ir, out_r.data());
         for (size_t l = 0; l < us.size(); ++l) {
             const double a = us[l][ir];
             const double* vl = vs[l].data();
@@ -295,7 +316,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         // of the sequential sums.
         pv.assign(us.size(), 0.0);
         if (fuse)
-            for (int64_t j = 0; j < nJ; ++j) rn[j] = entry(ib, j);
+            entry_row(ib, rn.data());
         const size_t np = us.size();
         size_t l = 0;
         for (; l + 4 <= np; l += 4) {
