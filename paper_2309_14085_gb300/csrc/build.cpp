@@ -948,7 +948,12 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
                          std::chrono::duration<double>(now - tp).count());
         tp = now;
     };
-    if (threads > 0) omp_set_num_threads(threads);
+    // the thread count applies to this construction only: restored on return
+    struct ThreadCount {
+        int prev;
+        explicit ThreadCount(int n) : prev(omp_get_max_threads()) { if (n > 0) omp_set_num_threads(n); }
+        ~ThreadCount() { omp_set_num_threads(prev); }
+    } thread_count(threads);
     build_tree(H.tree, points, N, d, leaf_size, kappa_forced, domain_lo, domain_side);
     if (H.tree.kappa > 20 / (d == 2 ? 1 : 1) || H.tree.nboxes(H.tree.kappa) > (int64_t(1) << 24))
         return "tree too deep (more than 2^24 leaves)";

@@ -128,3 +128,19 @@ def test_abi_arguments(tmp_path):
     assert L.h2_save(None, b"x") == -1
     A = _build(CASES[0])
     assert L.h2_save(A._h, os.fsencode(str(tmp_path / "no-such-dir" / "x.h2"))) == -1
+
+
+def test_construction_is_independent_of_the_thread_count(tmp_path):
+    """The whole construction (every pivot, operator and offset, as written by
+    h2_save) is the same with one host thread and with four: the parallel
+    loops split independent clusters and no sum crosses threads.  Bytes 60-67
+    hold the recorded build time."""
+    P = inputs.points(6000, 3, 98)
+    files = []
+    for threads in (1, 4):
+        A = H2Matrix(P, "invr", leaf_size=32, tol=1e-6, variant="h2plush", threads=threads,
+                     host_only=True)
+        files.append(str(tmp_path / f"t{threads}.h2"))
+        A.save(files[-1])
+    a, b = (open(f, "rb").read() for f in files)
+    assert len(a) == len(b) and a[:60] == b[:60] and a[68:] == b[68:]
