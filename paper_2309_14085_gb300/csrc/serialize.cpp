@@ -22,6 +22,7 @@
 namespace h2 {
 namespace {
 
+// the last byte is the format version: raise it whenever fields() changes
 constexpr char kMagic[8] = {'H', '2', 'S', 'T', 'A', 'R', '\0', '\1'};
 
 struct Writer {
