@@ -2,7 +2,8 @@
 h2_load gives the products of the saved one bit for bit (the same operators go
 through the same kernels), including M2L blocks formed on the device and RHS
 tiles on the tensor cores; a handle whose host operators were released cannot
-be saved."""
+be saved.  A converted copy (which copies the host state the same way) keeps
+working after its source is destroyed."""
 
 import pytest
 
@@ -31,3 +32,16 @@ def test_loaded_operators_give_the_saved_products(tmp_path):
     with pytest.raises(H2Error) as e:
         A.save(str(tmp_path / "released.h2"))
     assert e.value.status == "UNSUPPORTED"
+
+
+def test_converted_copy_outlives_its_source():
+    """h2_convert copies the host state; the copy's bases refer to its own
+    interaction lists, so its statistics stay valid after the source is gone."""
+    P = inputs.points(5000, 2, 99)
+    S = H2Matrix(P, "log2d", leaf_size=64, tol=1e-8)
+    pairs = S.info()["m2l_pairs"]
+    F = S.convert("f32")
+    S.close()
+    assert F.info()["m2l_pairs"] == pairs
+    x = torch.tensor(inputs.rhs(5000, 1, 100), device="cuda:0")
+    assert torch.isfinite(F.matvec(x)).all()
