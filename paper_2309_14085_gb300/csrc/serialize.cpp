@@ -4,12 +4,13 @@
 // rebuilt.  The paper has no counterpart; construction is its dominant cost
 // (the initialization times of §6's tables).
 //
-// Format: the 8 bytes "H2STAR\0\1", then every field in a fixed order, native
-// little-endian, 64-bit sizes; a vector is its length (int64) followed by its
-// elements.  A file is read with every length bounded by the bytes left, and
-// the loaded state is checked index by index against the buffers the device
-// kernels address (offsets, lengths, alignment), so a truncated or corrupted
-// file gives an error and never an out-of-range access.
+// Format: the 8 bytes "H2STAR\0" + version, then every field in a fixed
+// order, native little-endian, 64-bit sizes (a vector is its length, int64,
+// followed by its elements), then an 8-byte checksum of everything before it.
+// A file is read with every length bounded by the bytes left, its checksum is
+// compared, and the loaded state is checked index by index against the
+// buffers the device kernels address (offsets, lengths, alignment), so a
+// truncated or corrupted file gives an error and never an out-of-range access.
 
 #include <cstdio>
 #include <cstring>
@@ -23,13 +24,59 @@ namespace h2 {
 namespace {
 
 // the last byte is the format version: raise it whenever fields() changes
-constexpr char kMagic[8] = {'H', '2', 'S', 'T', 'A', 'R', '\0', '\1'};
+constexpr char kMagic[8] = {'H', '2', 'S', 'T', 'A', 'R', '\0', '\2'};
+
+// Checksum of the byte stream: the bytes as little-endian 64-bit words w_k,
+// h <- (h xor w_k) * P (the 64-bit FNV prime, odd, so every step is a
+// bijection of h and a change in any one word always changes the result),
+// then the length mixed in the same way.  Streamed, so chunk boundaries do
+// not matter.
+struct Checksum {
+    static constexpr uint64_t kPrime = 0x100000001b3ull;
+    uint64_t h = 0xcbf29ce484222325ull;
+    uint64_t total = 0;
+    unsigned char buf[8] = {};
+    int nbuf = 0;
+    void word(uint64_t w) { h = (h ^ w) * kPrime; }
+    void feed(const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        total += n;
+        if (nbuf > 0) {                       // complete the pending word first
+            const size_t take = std::min(n, size_t(8 - nbuf));
+            std::memcpy(buf + nbuf, b, take);
+            nbuf += int(take);
+            b += take;
+            n -= take;
+            if (nbuf < 8) return;
+            uint64_t w;
+            std::memcpy(&w, buf, 8);
+            word(w);
+            nbuf = 0;
+        }
+        for (; n >= 8; n -= 8, b += 8) { uint64_t w; std::memcpy(&w, b, 8); word(w); }
+        std::memcpy(buf, b, n);               // n < 8
+        nbuf = int(n);
+    }
+    uint64_t value() const {
+        Checksum c = *this;
+        if (c.nbuf > 0) {
+            std::memset(c.buf + c.nbuf, 0, size_t(8 - c.nbuf));
+            uint64_t w;
+            std::memcpy(&w, c.buf, 8);
+            c.word(w);
+        }
+        c.word(total);
+        return c.h;
+    }
+};
 
 struct Writer {
     std::FILE* f;
     bool ok = true;
+    Checksum sum;
     void raw(const void* p, size_t n) {
         if (ok && n > 0 && std::fwrite(p, 1, n, f) != n) ok = false;
+        sum.feed(p, n);
     }
     template <class T> void pod(const T& v) {
         static_assert(std::is_trivially_copyable<T>::value, "plain data only");
@@ -51,12 +98,14 @@ struct Writer {
 
 struct Reader {
     std::FILE* f;
-    int64_t left;
+    int64_t left;                     // bytes of fields left (the checksum excluded)
     bool ok = true;
+    Checksum sum;
     void raw(void* p, size_t n) {
         if (!ok) return;
         if (int64_t(n) > left || (n > 0 && std::fread(p, 1, n, f) != n)) { ok = false; return; }
         left -= int64_t(n);
+        sum.feed(p, n);
     }
     template <class T> void pod(T& v) { raw(&v, sizeof(T)); }
     int64_t count(size_t min_bytes_each) {
@@ -419,6 +468,8 @@ std::string save_host(const Host& H, const char* path) {
     Writer w{f};
     w.raw(kMagic, sizeof(kMagic));
     fields(w, H);
+    const uint64_t check = w.sum.value();
+    if (w.ok && std::fwrite(&check, 1, sizeof(check), f) != sizeof(check)) w.ok = false;
     const bool closed = std::fclose(f) == 0;
     if (!w.ok || !closed) {
         std::remove(path);
@@ -433,22 +484,30 @@ std::string load_host(Host& H, const char* path) {
     int64_t size = -1;
     if (std::fseek(f, 0, SEEK_END) == 0) size = int64_t(std::ftell(f));
     std::rewind(f);
-    if (size < int64_t(sizeof(kMagic))) {
+    if (size < int64_t(sizeof(kMagic) + 8)) {
         std::fclose(f);
         return "not an H2* checkpoint (too short)";
     }
-    Reader r{f, size};
+    Reader r{f, size - 8};
     char magic[8] = {};
     r.raw(magic, sizeof(magic));
-    if (!r.ok || std::memcmp(magic, kMagic, sizeof(kMagic)) != 0) {
+    if (!r.ok || std::memcmp(magic, kMagic, sizeof(kMagic) - 1) != 0) {
         std::fclose(f);
         return "not an H2* checkpoint (magic)";
     }
+    if (magic[7] != kMagic[7]) {
+        std::fclose(f);
+        return "checkpoint format version " + std::to_string(int(magic[7])) + ", this library reads " +
+               std::to_string(int(kMagic[7]));
+    }
     fields(r, H);
     const int64_t left = r.left;
+    uint64_t check = 0;
+    const bool got = r.ok && left == 0 && std::fread(&check, 1, sizeof(check), f) == sizeof(check);
     std::fclose(f);
     if (!r.ok) return "truncated or corrupted checkpoint";
     if (left != 0) return "trailing bytes after the checkpoint";
+    if (!got || check != r.sum.value()) return "checkpoint checksum mismatch (corrupted file)";
     relink_lists(H);
     std::string e = validate(H);
     if (!e.empty()) return "inconsistent checkpoint: " + e;
