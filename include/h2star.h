@@ -173,9 +173,9 @@ int h2_convert(h2_handle src, int storage, h2_handle* out);
  * current CUDA device in the saved storage, with the same products as the
  * saved handle's; M2L blocks formed on the device (m2l_mode 2) are formed again
  * there.  A loaded file is bounds-checked field by field (every length against
- * the bytes left) and then index by index against the buffers the device
- * kernels address, so a truncated or corrupted file is an error, never an
- * out-of-range access.
+ * the bytes left), its trailing 64-bit checksum is compared, and the state is
+ * checked index by index against the buffers the device kernels address, so a
+ * truncated or corrupted file is an error, never an out-of-range access.
  * Errors: H2_E_INVALID_ARG (NULL argument, file not readable or writable, not
  * a checkpoint, truncated or inconsistent), H2_E_UNSUPPORTED (h2_save of a
  * handle whose host operators were released), H2_E_OOM, H2_E_NO_DEVICE,
