@@ -202,8 +202,13 @@ void build_lists(const Tree& t, Lists& L) {
 // Partially pivoted ACA (§3.6), in the reading documented with the oracle:
 // first row first; residual row; column pivot = first argmax over unused
 // columns; zero row -> next unused row; residual column; incremental
-// Frobenius norm; stop after accepting a pivot with |u||v| <= eps ||S||_F;
+// Frobenius norm; stop once |u||v| <= eps ||S||_F has held for kAcaStopStreak
+// accepted pivots in a row (a failing pivot resets the count: one cross
+// under-estimates the remaining error of the large, nearly singular
+// vertex-sharing search blocks of §5.1.1, and stopping at the first pass left
+// H2*(b+t) an order of magnitude less accurate than the paper's tables);
 // next row = first argmax of |u| over unused rows.
+constexpr int kAcaStopStreak = 3;
 struct AcaResult {
     std::vector<int> rows, cols;
     std::vector<std::vector<double>> us, vs;   // kept only when requested
@@ -255,6 +260,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
     std::vector<double> r(nJ), rn(nJ), u(nI), pv;
     double S2 = 0.0;
     int64_t i = 0;
+    int streak = 0;
     const int64_t kmax = std::min(nI, nJ);
     auto next_free_row = [&]() -> int64_t {
         for (int64_t a = 0; a < nI; ++a)
@@ -383,7 +389,11 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         vs.emplace_back(std::move(v));
         out.rows.push_back(int(i));
         out.cols.push_back(int(jb));
-        if (std::sqrt(uu) * std::sqrt(vv) <= eps * std::sqrt(std::max(S2, 0.0))) break;
+        if (std::sqrt(uu) * std::sqrt(vv) <= eps * std::sqrt(std::max(S2, 0.0))) {
+            if (++streak >= kAcaStopStreak) break;
+        } else {
+            streak = 0;
+        }
         if (fuse) {
             i = ib;
             std::swap(r, rn);
