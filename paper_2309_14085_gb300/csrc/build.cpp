@@ -201,14 +201,20 @@ void build_lists(const Tree& t, Lists& L) {
 // ---------------------------------------------------------------------------
 // Partially pivoted ACA (§3.6), in the reading documented with the oracle:
 // first row first; residual row; column pivot = first argmax over unused
-// columns; zero row -> next unused row; residual column; incremental
-// Frobenius norm; stop once |u||v| <= eps ||S||_F has held for kAcaStopStreak
-// accepted pivots in a row (a failing pivot resets the count: one cross
-// under-estimates the remaining error of the large, nearly singular
-// vertex-sharing search blocks of §5.1.1, and stopping at the first pass left
-// H2*(b+t) an order of magnitude less accurate than the paper's tables);
-// next row = first argmax of |u| over unused rows.
-constexpr int kAcaStopStreak = 3;
+// columns; a row whose largest residual is at most kAcaNoise times the largest
+// pivot so far (rounding: coincident points, a block captured to full rank)
+// is spent -> next unused row; residual column; incremental Frobenius norm;
+// next row = first argmax of |u| over unused rows.  Stopping: the first cross
+// k with |u||v| <= eps ||S||_F whose next kAcaLookahead crosses pass the test
+// too; crosses 1..k are kept and the look-ahead ones dropped (one cross
+// under-estimates the remaining error of the large, nearly singular search
+// blocks -- stopping at the first pass left H2*(b+t) an order of magnitude
+// less accurate than the paper's tables -- while keeping the look-ahead
+// crosses, which lie below the tolerance, makes the interpolation operators
+// ill-conditioned).
+constexpr int kAcaLookahead = 2;
+constexpr double kAcaNoise = 0x1p-46;
+
 struct AcaResult {
     std::vector<int> rows, cols;
     std::vector<std::vector<double>> us, vs;   // kept only when requested
@@ -260,7 +266,8 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
     std::vector<double> r(nJ), rn(nJ), u(nI), pv;
     double S2 = 0.0;
     int64_t i = 0;
-    int streak = 0;
+    double pmax = 0.0;
+    int64_t first = -1;     // crosses kept if the running look-ahead confirms the stop
     const int64_t kmax = std::min(nI, nJ);
     auto next_free_row = [&]() -> int64_t {
         for (int64_t a = 0; a < nI; ++a)
@@ -285,12 +292,13 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
             const double a = col_used[j] ? -1.0 : std::fabs(r[j]);
             if (a > best) { best = a; jb = j; }
         }
-        if (best <= 0.0) {
+        if (best <= kAcaNoise * pmax || best <= 0.0) {
             i = next_free_row();
             if (i < 0) break;
             fresh_row(i, r);
             continue;
         }
+        pmax = std::max(pmax, best);
         const double piv = r[jb];
         std::vector<double> v(nJ);
         for (int64_t j = 0; j < nJ; ++j) v[j] = r[j] / piv;
@@ -390,9 +398,10 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         out.rows.push_back(int(i));
         out.cols.push_back(int(jb));
         if (std::sqrt(uu) * std::sqrt(vv) <= eps * std::sqrt(std::max(S2, 0.0))) {
-            if (++streak >= kAcaStopStreak) break;
+            if (first < 0) first = int64_t(out.rows.size());
+            if (int64_t(out.rows.size()) - first >= kAcaLookahead) break;
         } else {
-            streak = 0;
+            first = -1;
         }
         if (fuse) {
             i = ib;
@@ -401,6 +410,14 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
             i = next_free_row();
             if (i < 0) break;
             fresh_row(i, r);
+        }
+    }
+    if (first >= 0) {
+        out.rows.resize(size_t(first));
+        out.cols.resize(size_t(first));
+        if (us.size() > size_t(first)) {
+            us.resize(size_t(first));
+            vs.resize(size_t(first));
         }
     }
     if (!keep) {
