@@ -45,7 +45,7 @@ def test_batch_equals_individual_products(storage):
     got = B.matvec([torch.tensor(inputs.rhs(s[1], s[2], 4000 + k).reshape(s[1], s[2]), device="cuda:0")
                     for k, s in enumerate(specs)])[1].cpu().numpy()
     if storage == "f64":
-        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
     else:
         # every stored entry rounded to a 24 / 48-bit significand: 64 u (|K||q|)_i
         u = 2.0 ** -24 if storage == "f32" else 2.0 ** -48
