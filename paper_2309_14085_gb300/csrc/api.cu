@@ -55,7 +55,25 @@ struct DevRowTasks {
     int max_rows = 0;             // largest task (rows)
     int64_t *dst = nullptr, *aoff = nullptr, *seg_ptr = nullptr, *seg_off = nullptr;
     int32_t *rows = nullptr, *kpad = nullptr, *seg_len = nullptr, *seg_col = nullptr;
+    // per task, packed for one 48-byte load of the tensor-core kernel:
+    // aoff, dst, first segment, segment count, rows, kpad
+    int64_t* meta = nullptr;
 };
+
+// the packed task records of DevRowTasks::meta
+std::vector<int64_t> task_meta(const h2::RowTasks& R) {
+    std::vector<int64_t> m(size_t(R.size()) * 6);
+    for (int64_t k = 0; k < R.size(); ++k) {
+        int64_t* e = m.data() + k * 6;
+        e[0] = R.aoff[k];
+        e[1] = R.dst[k];
+        e[2] = R.seg_ptr[k];
+        e[3] = R.seg_ptr[k + 1] - R.seg_ptr[k];
+        e[4] = R.rows[k];
+        e[5] = R.kpad[k];
+    }
+    return m;
+}
 
 struct h2_handle_s {
     h2::Host host;
@@ -218,6 +236,7 @@ int upload_rows(h2_handle h, DevRowTasks& D, const h2::RowTasks& R) {
     H2_TRY(dev_upload(h, &D.kpad, R.kpad));
     H2_TRY(dev_upload(h, &D.seg_len, R.seg_len));
     H2_TRY(dev_upload(h, &D.seg_col, R.seg_col));
+    H2_TRY(dev_upload(h, &D.meta, task_meta(R)));
     D.max_rows = R.rows.empty() ? 0 : *std::max_element(R.rows.begin(), R.rows.end());
     return H2_OK;
 }
@@ -326,12 +345,12 @@ int tc_setup_nt(h2_handle h, int nsm, int smem_sm, int slot) {
                                  tc_smem<S, NT>()));
     int occ = 0;
     H2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h2::k_rowgemm_tc<S, NT>,
-                                                          h2::tc::kThreads, tc_smem<S, NT>()));
+                                                          h2::tc::kThreadsWs, tc_smem<S, NT>()));
     cudaFuncAttributes fa;
     H2_CUDA(cudaFuncGetAttributes(&fa, h2::k_rowgemm_tc<S, NT>));
     const int by_smem = smem_sm / (tc_smem<S, NT>() + 1024);
-    const int by_tmem = 512 / (NT < 32 ? 32 : NT);
-    const int by_regs = 65536 / (std::max(fa.numRegs, 1) * h2::tc::kThreads);
+    const int by_tmem = 512 / int(h2::tc::Plan<S, NT>::kCols);
+    const int by_regs = 65536 / (std::max(fa.numRegs, 1) * h2::tc::kThreadsWs);
     h->tc_occupancy[slot] = occ;
     h->tc_blocks[slot] = std::max(1, std::min(std::min(by_smem, by_tmem), by_regs)) * nsm;
     return H2_OK;
@@ -359,17 +378,14 @@ void launch_rows_tc(const DevRowTasks& R, const void* ops, void* vec, cudaStream
         const int slot = nt == 64 ? 0 : nt == 32 ? 1 : 2;
         const unsigned n = unsigned(std::min<int64_t>(R.n, blocks[slot]));
         if (nt == 64)
-            h2::k_rowgemm_tc<S, 64><<<n, h2::tc::kThreads, tc_smem<S, 64>(), s>>>(
-                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col, o, v,
-                accumulate, nrhs, c0, err);
+            h2::k_rowgemm_tc<S, 64><<<n, h2::tc::kThreadsWs, tc_smem<S, 64>(), s>>>(
+                R.n, R.meta, R.seg_off, R.seg_len, R.seg_col, o, v, accumulate, nrhs, c0, err);
         else if (nt == 32)
-            h2::k_rowgemm_tc<S, 32><<<n, h2::tc::kThreads, tc_smem<S, 32>(), s>>>(
-                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col, o, v,
-                accumulate, nrhs, c0, err);
+            h2::k_rowgemm_tc<S, 32><<<n, h2::tc::kThreadsWs, tc_smem<S, 32>(), s>>>(
+                R.n, R.meta, R.seg_off, R.seg_len, R.seg_col, o, v, accumulate, nrhs, c0, err);
         else
-            h2::k_rowgemm_tc<S, 16><<<n, h2::tc::kThreads, tc_smem<S, 16>(), s>>>(
-                R.n, R.dst, R.rows, R.kpad, R.aoff, R.seg_ptr, R.seg_off, R.seg_len, R.seg_col, o, v,
-                accumulate, nrhs, c0, err);
+            h2::k_rowgemm_tc<S, 16><<<n, h2::tc::kThreadsWs, tc_smem<S, 16>(), s>>>(
+                R.n, R.meta, R.seg_off, R.seg_len, R.seg_col, o, v, accumulate, nrhs, c0, err);
     }
 }
 
@@ -1679,6 +1695,7 @@ int bupload_rows(h2_batch b, DevRowTasks& D, const h2::RowTasks& R) {
     H2_TRY(bupload(b, &D.kpad, R.kpad));
     H2_TRY(bupload(b, &D.seg_len, R.seg_len));
     H2_TRY(bupload(b, &D.seg_col, R.seg_col));
+    H2_TRY(bupload(b, &D.meta, task_meta(R)));
     D.rw = 4;
     D.max_rows = R.rows.empty() ? 0 : *std::max_element(R.rows.begin(), R.rows.end());
     return H2_OK;

@@ -4,30 +4,19 @@
 // i < rows and an NT-column tile c of the RHS; with NT = 64 every operator
 // entry streamed from HBM feeds 64 multiply-adds, so the contraction runs on the
 // 5th-generation tensor cores instead of re-streaming the operators per
-// CUDA-core tile.
+// CUDA-core tile.  The kernel (k_rowgemm_tc, below) is warp-specialised:
+// producer warps fill a ring of shared-memory stages with cp.async copies of
+// the operator rows and gathered coefficients, one thread issues tcgen05.mma
+// into one of two TMEM accumulators, epilogue warps drain the other.  fp32
+// operators run as a 3-term tf32 product (hi / lo split of both operands), so
+// the result carries ~2^-21 relative rounding per product instead of tf32's
+// 2^-11; bf16 operators run as one bf16 product.
 //
-// Per CTA (256 threads = 8 warps; persistent: tasks blockIdx.x, + gridDim.x, ...):
-//   * warp 0 allocates NT columns of tensor memory (TMEM) for the 128 x NT fp32
-//     accumulator once, and the chunk mbarriers are initialised once;
-//   * the K dimension runs in chunks of 128 bytes per row (64 bf16 or 32 fp32
-//     entries); all threads stage a chunk of A (the task's rows only: rows of
-//     the 128-row MMA beyond them hold stale data and produce accumulator rows
-//     that are never read) and of X (NT columns, gathered from the task's coefficient segments,
-//     converted to the MMA input type) into shared memory in the canonical
-//     no-swizzle K-major layout: 8-row x 16-byte core matrices, 128 B apart
-//     along K (leading byte offset) and 1024 B apart along M / N (stride byte
-//     offset);
-//   * thread 0 issues four tcgen05.mma per chunk (K = 32 bytes each) and
-//     commits them to the chunk's mbarrier; two chunk buffers alternate, and
-//     each thread issues the global loads of chunk g + 1 (into registers) right
-//     after storing chunk g, so they fly during the barrier and the MMAs;
-//   * warp w reads accumulator rows 32 (w mod 4) .. + 31, columns of half
-//     w / 4, back with tcgen05.ld and adds them to Y (fp32).
-// Staging maps a warp onto 8 rows (or RHS columns) x 4 words of one 16-byte
-// core-matrix slot, so its shared-memory stores hit all 32 banks once; each
-// thread issues all its global loads of a chunk before its stores.
-// Every mbarrier wait is bounded: on expiry the CTA records an error code in
-// *err, waits (bounded) for its MMAs in flight, frees its TMEM and returns.
+// Shared-memory tiles use the canonical no-swizzle K-major layout: 8-row x
+// 16-byte core matrices, 128 B apart along K (leading byte offset) and 1024 B
+// apart along M / N (stride byte offset).  Every mbarrier wait is bounded: on
+// expiry the CTA records an error code in *err, waits (bounded) for its MMAs in
+// flight, frees its TMEM and returns.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -37,10 +26,7 @@
 namespace h2 {
 namespace tc {
 
-constexpr int kThreads = 256;           // 8 warps
 constexpr int kRowsTile = 128;              // MMA M
-constexpr int kChunkBytes = 128;            // K bytes per row per chunk
-constexpr int kATileBytes = kRowsTile * kChunkBytes;
 constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before giving up
 constexpr int kErrTimeout = 1;
 
@@ -127,88 +113,184 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  ::"r"(smem_u32(bar)) : "memory");
 }
 
-// 32 lanes x 32 bits, 8 consecutive columns: thread t of the warp receives
-// row (lane base + t), columns col .. col + 7
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-    uint32_t r[8];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+
+// asynchronous global -> shared copies (cp.async) of 16 bytes (L2 only), 8 or 4
+// bytes; bytes past src_bytes (0 .. size) are zero-filled and not read
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes) : "memory");
+}
+// one arrival on `bar` once every cp.async this thread issued so far has
+// landed (the barrier's count includes these arrivals)
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// barrier `id` (1..15) among `n` threads of the CTA (a multiple of 32)
+__device__ __forceinline__ void named_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// byte offset of (row r, K byte kb) in a staged tile (no-swizzle K-major)
-__device__ __forceinline__ uint32_t tile_off(int r, int kb) {
-    return uint32_t((r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
+// x = hi + lo with hi on the tf32 grid (10 fraction bits, rounded to nearest)
+// and lo = x - hi exact in fp32 (|lo| <= 2^-11 |x|): the terms of the 3-term
+// tf32 product a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (the dropped a_lo b_lo
+// and the tf32 rounding of the lo terms leave ~2^-21 of |a b|)
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+    hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+    lo = x - hi;
 }
 
-template <typename S> struct In;
-template <> struct In<__nv_bfloat16> {
-    using T = __nv_bfloat16;                 // MMA input element
-    static constexpr bool BF = true;
-    static constexpr uint32_t FMT = 1;
-    static constexpr int KPW = 2;            // K entries per 32-bit word
-    // two consecutive K entries of one column -> one word (lower K in the low half)
-    __device__ static uint32_t pack(const float (&x)[2]) {
-        const __nv_bfloat162 b = __floats2bfloat162_rn(x[0], x[1]);
-        return *reinterpret_cast<const uint32_t*>(&b);
-    }
-};
-template <> struct In<float> {
-    using T = float;                         // tf32: fp32 container, tf32 multiply
-    static constexpr bool BF = false;
-    static constexpr uint32_t FMT = 2;
-    static constexpr int KPW = 1;
-    __device__ static uint32_t pack(const float (&x)[1]) { return __float_as_uint(x[0]); }
+// Warp roles of the block-row GEMM: 4 producer warps, 4 epilogue warps (warp
+// 4 + q reads TMEM lanes 32 q .. 32 q + 31), 1 MMA warp (TMEM owner).
+constexpr int kProducerWarps = 4;
+constexpr int kProducerThreads = 32 * kProducerWarps;
+constexpr int kEpiThreads = 128;
+constexpr int kMmaWarp = 8;
+constexpr int kThreadsWs = 32 * 9;
+constexpr int kCB = 64;                         // K bytes per row per pipeline chunk
+
+// byte offset of (row r, K byte kb < kCB) in a chunk tile (no-swizzle K-major:
+// 8-row x 16-byte core matrices, 128 B apart along K, 8 kCB apart along M / N)
+__device__ __forceinline__ uint32_t ctile_off(int r, int kb) {
+    return uint32_t((r >> 3) * (8 * kCB) + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
+}
+
+// Shared-memory plan of k_rowgemm_tc<S, NT>.  A stage holds one K chunk:
+// fp32 storage (3-term tf32 product) A_hi, A_lo, B_hi, B_lo and the raw
+// gathered coefficients; bf16 storage A, B and the raw coefficients.
+template <typename S, int NT>
+struct Plan {
+    static constexpr bool kSplit = sizeof(S) == 4;
+    static constexpr int kES = int(sizeof(S));
+    static constexpr int kKC = kCB / kES;                     // K entries per chunk
+    static constexpr int kATile = kRowsTile * kCB;
+    static constexpr int kBTile = NT * kCB;
+    // raw coefficients [k][n], rows of NT + 8 floats: the 4 K rows a warp
+    // reads at once fall on disjoint banks
+    static constexpr int kRawLd = NT + 8;
+    static constexpr int kBRaw = kKC * kRawLd * 4;
+    static constexpr int kStage = (kSplit ? 2 : 1) * (kATile + kBTile) + kBRaw;
+    static constexpr int kStages = kSplit ? 3 : 4;
+    static constexpr int kLag = kStages - 2;                  // chunks in flight past the published one
+    // per producer warp: the source of every K entry of its current chunk, and
+    // the segments (column, length, offset) of its current task, up to kSegCap
+    // (a task with more searches global memory)
+    static constexpr int kSegCap = 96;
+    static constexpr int kTabOff = kStages * kStage;
+    static constexpr int kSegOff = kTabOff + kProducerWarps * kKC * 8;
+    // the tile ring: producer warp 0 posts every tile (and zero-filled task) in
+    // order, the MMA thread and the epilogue read it: {y offset, chunks, rows}
+    static constexpr int kRing = 8;
+    static constexpr int kRingOff = kSegOff + kProducerWarps * kSegCap * 16;
+    static constexpr int kBarOff = kRingOff + kRing * 16;
+    // landed[kStages], full[kStages], empty[kStages], acc_full[2], acc_empty[2],
+    // info[kRing], info_free[kRing]; then the TMEM address and the failure flag
+    static constexpr int kNBar = 3 * kStages + 4 + 2 * kRing;
+    static constexpr int kBytes = kBarOff + kNBar * 8 + 16;
+    static constexpr uint32_t kCols = 2 * NT < 32 ? 32 : 2 * NT;   // two accumulators
+    static_assert(kStage % 128 == 0 && kTabOff % 16 == 0, "stage alignment");
 };
 
 }  // namespace tc
 
-// Block-row GEMM on tensor cores; S = stored operator type (bf16 or fp32),
-// coefficients are fp32.  Dynamic shared memory: tc_smem_bytes<S, NT>().
+// Block-row GEMM on tensor cores, warp-specialised: Y[dst + i][c0 + c] (+)=
+// sum_k A[i * kpad + k] X[k][c0 + c] for every task of the list, an NT-column
+// RHS tile, S = stored operator type (fp32: 3-term tf32 product; bf16), fp32
+// coefficients.  Persistent CTAs (two per SM) take tasks blockIdx.x,
+// + gridDim.x, ...; a task's rows run in tiles of 128 (the MMA's M) and its K
+// in chunks of kCB = 64 bytes per row, through a ring of tc::Plan::kStages
+// shared-memory stages:
+//   producers  (warps 0-3, each on its own over its quarter of every chunk):
+//              the source table of the chunk's K entries (from the task's
+//              segments, copied to shared memory once per task); cp.async of
+//              the operator rows into the stage's canonical no-swizzle K-major
+//              tile (bytes past kpad zero-filled, rows past the task's left
+//              stale: their accumulator rows are never read) and of the
+//              coefficient rows, 16 bytes of the RHS tile at a time, into a raw
+//              [k][n] tile, each thread then arriving on landed[s] when its
+//              copies land; kLag chunks later (landed[s] complete) the fp32
+//              tiles are split into tf32 hi / lo terms, the coefficients
+//              transposed into the K-major B tile (bf16 pairs, or hi / lo), and
+//              the stage published on full[s].  A stage is refilled after the
+//              MMAs that read it committed to empty[s].
+//   MMA thread (warp 8, lane 0): per chunk 2 K-steps of 32 bytes, each one
+//              tcgen05.mma (bf16) or three (a_hi b_hi + a_hi b_lo + a_lo b_hi),
+//              committed to empty[s]; the tile's last commit goes to acc_full[a]
+//              of one of two TMEM accumulators, so the next tile's MMAs overlap
+//              the epilogue of this one.
+//   epilogue   (warps 4-7): tcgen05.ld of accumulator rows 32 (w - 4) .. + 31,
+//              added to / stored in Y; then acc_empty[a].
+// Every mbarrier wait is bounded; an expired wait records kErrTimeout in *err
+// and the CTA winds down (each producer warp at its next chunk, the others at
+// their next expired wait), waits (bounded) for its MMAs in flight and frees
+// its TMEM.  Dynamic shared memory: tc::Plan<S, NT>::kBytes.
 template <typename S, int NT>
 __host__ __device__ constexpr int tc_smem_bytes() {
-    return 2 * (tc::kATileBytes + NT * tc::kChunkBytes) + 2 * (tc::kChunkBytes / int(sizeof(S))) * 8 + 64;
+    return tc::Plan<S, NT>::kBytes;
 }
 
 template <typename S, int NT>
-__global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
-    int64_t ntask, const int64_t* __restrict__ dst, const int32_t* __restrict__ rows,
-    const int32_t* __restrict__ kpad, const int64_t* __restrict__ aoff,
-    const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_off,
+__global__ void __launch_bounds__(tc::kThreadsWs, 2) k_rowgemm_tc(
+    int64_t ntask, const int64_t* __restrict__ meta, const int64_t* __restrict__ seg_off,
     const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_col,
     const S* __restrict__ ops, float* __restrict__ vec, int accumulate, int nrhs, int c0,
     int* __restrict__ err) {
-    using In = tc::In<S>;
+    using P = tc::Plan<S, NT>;
     static_assert(NT == 16 || NT == 32 || NT == 64, "RHS tile");
-    constexpr int ES = int(sizeof(S));
-    constexpr int KC = tc::kChunkBytes / ES;            // K entries per chunk
-    constexpr int KPW = In::KPW;
-    constexpr int kBTileBytes = NT * tc::kChunkBytes;
-    constexpr int kBufBytes = tc::kATileBytes + kBTileBytes;
-    constexpr uint32_t kCols = NT < 32 ? 32 : NT;       // TMEM columns (power of 2, >= 32)
-    constexpr uint32_t kIdesc = tc::instr_desc(In::FMT, tc::kRowsTile, NT);
-    constexpr int kAUnits = tc::kRowsTile * 16;         // 8-byte units of a full A tile
-    constexpr int kAPer = kAUnits / tc::kThreads;       // per thread
-    constexpr int kBItems = KC * NT / KPW;              // 32-bit words of a B tile
-    constexpr int kBPer = kBItems / tc::kThreads;
-    static_assert(kBItems % tc::kThreads == 0 && kAUnits % tc::kThreads == 0, "staging split");
+    constexpr bool SPLIT = P::kSplit;
+    constexpr int KC = P::kKC, NS = P::kStages, CB = tc::kCB, RING = P::kRing;
+    constexpr int UPR = CB / (SPLIT ? 16 : 8);                         // A copy units per row
+    constexpr int SPG = UPR / 4;                                       // warp steps per row group
+    constexpr int AUNITS = tc::kRowsTile * UPR / tc::kProducerThreads;  // per thread
+    constexpr int RTOTAL = KC * (NT / 4);                              // raw 16-byte units per chunk
+    constexpr int RUNITS = (RTOTAL + tc::kProducerThreads - 1) / tc::kProducerThreads;
+    constexpr int BWORDS = NT * (CB / 4) / tc::kProducerThreads;      // B tile words per thread
+    static_assert(BWORDS >= 1 && BWORDS * tc::kProducerThreads == NT * (CB / 4), "producer split");
+    constexpr uint32_t kIdesc = tc::instr_desc(SPLIT ? 2u : 1u, tc::kRowsTile, NT);
     extern __shared__ __align__(1024) uint8_t smem[];
-    int64_t* tab = reinterpret_cast<int64_t*>(smem + 2 * kBufBytes);   // [2][KC] sources
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes + 2 * KC * 8);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
-    int* fail = reinterpret_cast<int*>(tmem_slot + 1);
+    int64_t* tab = reinterpret_cast<int64_t*>(smem + P::kTabOff);
+    int64_t* ring = reinterpret_cast<int64_t*>(smem + P::kRingOff);   // [RING][2]
+    uint64_t* landed = reinterpret_cast<uint64_t*>(smem + P::kBarOff);
+    uint64_t* full = landed + NS;
+    uint64_t* empty = full + NS;
+    uint64_t* acc_full = empty + NS;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* info = acc_empty + 2;
+    uint64_t* info_free = info + RING;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(info_free + RING);
+    volatile int* fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     if (int64_t(blockIdx.x) >= ntask) return;
-    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    if (warp == 0) tc::tmem_alloc(tmem_slot, kCols);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ncols = min(NT, nrhs - c0);
+    if (warp == tc::kMmaWarp) tc::tmem_alloc(tmem_slot, P::kCols);
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        for (int i = 0; i < NS; ++i) {
+            tc::mbar_init(&landed[i], tc::kProducerThreads);
+            tc::mbar_init(&full[i], tc::kProducerThreads);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], tc::kEpiThreads);
+        }
+        for (int i = 0; i < RING; ++i) {
+            tc::mbar_init(&info[i], 1);
+            tc::mbar_init(&info_free[i], tc::kEpiThreads + 1);
+        }
         *fail = 0;
         tc::fence_async_smem();
     }
@@ -216,144 +298,410 @@ __global__ void __launch_bounds__(tc::kThreads, 3) k_rowgemm_tc(
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    uint32_t g = 0;                                      // chunks issued by this CTA
-    bool ok = true;
-    uint2 av[kAPer];                                     // staged loads of the next chunk
-    float bv[kBPer][KPW];
+    auto on_fail = [&]() {
+        *fail = 1;
+        atomicExch(err, tc::kErrTimeout);
+    };
 
-    for (int64_t t = blockIdx.x; t < ntask && ok; t += gridDim.x) {
-        const int kp = kpad[t];
-        const int nr = rows[t];
-        const int64_t e0 = seg_ptr[t], e1 = seg_ptr[t + 1];
-        const S* Am = ops + aoff[t];
-        float* y = vec + dst[t] * nrhs + c0;
-        const int ncols = min(NT, nrhs - c0);
-        const int nchunk = (kp + KC - 1) / KC;
-        if (nchunk == 0) {                               // no columns: y = 0 (or unchanged)
-            for (int j = tid; j < nr * ncols && !accumulate; j += tc::kThreads)
-                y[int64_t(j / ncols) * nrhs + (j % ncols)] = 0.0f;
-        }
-        // source coefficient of every K entry of chunk ch (-1: zero), into table slot
-        auto build_table = [&](int ch, int slot) {
-            if (tid < KC) {
-                const int k = ch * KC + tid;
-                int64_t si = -1;
-                for (int64_t e = e0; e < e1; ++e) {
-                    const int sc = seg_col[e];
-                    if (k < sc) break;
-                    if (k < sc + seg_len[e]) { si = seg_off[e] + (k - sc); break; }
+    if (warp < tc::kProducerWarps) {
+        // ------------------------------------------------------------ producers
+        // Each producer warp runs the chunk sequence on its own (its quarter of
+        // the units of every chunk): lane 0 waits for the stage, the warp builds
+        // its table, issues its copies, and publishes its chunk kLag back; the
+        // 128 producer threads arrive on full[s].  The task records are loaded
+        // two tasks ahead and the segments of the next task are copied while
+        // the current one runs; warp 0 posts every tile to the ring.
+        const int pw = warp, ptid = tid;
+        int64_t* wtab = tab + pw * KC;
+        const bool raw16 = (nrhs % 4 == 0) && (c0 % 4 == 0);   // 16-byte aligned coefficient rows
+        struct Task {
+            int64_t aoff, dst, e0, nseg, rows, kpad;
+        };
+        auto load_task = [&](int64_t t) -> Task {
+            Task k{0, 0, 0, 0, 0, 0};
+            if (t < ntask) {
+                const longlong2* m = reinterpret_cast<const longlong2*>(meta + t * 6);
+                const longlong2 a = __ldg(m), b = __ldg(m + 1), c = __ldg(m + 2);
+                k = Task{a.x, a.y, b.x, b.y, c.x, c.y};
+            }
+            return k;
+        };
+        // the warp's segment copy in shared memory
+        int32_t* const wcol = reinterpret_cast<int32_t*>(smem + P::kSegOff) + pw * P::kSegCap * 4;
+        int32_t* const wlen = wcol + P::kSegCap;
+        int64_t* const woff = reinterpret_cast<int64_t*>(wlen + P::kSegCap);
+        constexpr int SPL = P::kSegCap / 32;               // segments per lane
+        struct Segs {
+            int32_t col[SPL], len[SPL];
+            int64_t off[SPL];
+        };
+        // global loads of task k's segments into registers (issued a task ahead)
+        auto load_segs = [&](const Task& k, Segs& r) {
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                const int e = lane + 32 * j;
+                if (k.rows > 0 && k.kpad > 0 && k.nseg <= P::kSegCap && e < k.nseg) {
+                    r.col[j] = __ldg(seg_col + k.e0 + e);
+                    r.len[j] = __ldg(seg_len + k.e0 + e);
+                    r.off[j] = __ldg(seg_off + k.e0 + e);
                 }
-                tab[slot * KC + tid] = si;
             }
         };
-        // global loads of chunk ch into registers (A: 8 rows x 4 units per warp;
-        // X: column c_lo = lane & 7 of a group of 8, word (lane >> 3) & 3 of the slot)
-        auto load_chunk = [&](int m0, int mt, int ch, int slot) {
+        auto store_segs = [&](const Task& k, const Segs& r) {
+            __syncwarp();                                  // the previous task's searches done
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                const int e = lane + 32 * j;
+                if (k.nseg <= P::kSegCap && e < k.nseg) {
+                    wcol[e] = r.col[j];
+                    wlen[e] = r.len[j];
+                    woff[e] = r.off[j];
+                }
+            }
+            __syncwarp();
+        };
+        const int64_t G = gridDim.x;
+        int64_t t = blockIdx.x;
+        Task cur = load_task(t), nx1 = load_task(t + G), nx2 = load_task(t + 2 * G);
+        Segs pre;
+        load_segs(cur, pre);
+        int nseg = 0, kp = 0, nr = 0, nchunk = 0, m0 = 0, ch = -1;
+        const S* Am = ops;
+        uint32_t posted = 0;                               // ring entries (warp 0)
+        bool ok = true;
+        // warp 0, lane 0: post a ring entry {y offset, chunks (0: zero-fill, -1: end), rows}
+        // (called by every lane of every producer warp: `ok` stays warp-uniform)
+        auto post = [&](int64_t yoff, int nch, int rows) {
+            if (pw != 0) return;
+            if (lane == 0 && ok) {
+                const uint32_t e = posted++;
+                const int slot = int(e % RING);
+                if (e >= RING && !tc::mbar_wait(&info_free[slot], ((e / RING) - 1) & 1, tc::kWaitLimit)) {
+                    on_fail();
+                    ok = false;
+                } else {
+                    ring[slot * 2] = yoff;
+                    ring[slot * 2 + 1] = (int64_t(nch) << 32) | uint32_t(rows);
+                    tc::mbar_arrive(&info[slot]);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+        };
+        // move on to the task after `cur`: its segments landed; prefetch the one after
+        auto next_task = [&]() {
+            cur = nx1;
+            nx1 = nx2;
+            t += G;
+            nx2 = load_task(t + 2 * G);
+        };
+        // the next chunk of this CTA's sequence (false when none is left)
+        bool entered = false;
+        auto advance = [&]() -> bool {
+            if (nchunk > 0 && ++ch < nchunk) return true;
+            ch = 0;
+            if (nchunk > 0 && (m0 += tc::kRowsTile) < nr) {
+                post((cur.dst + m0) * nrhs + c0, nchunk, min(tc::kRowsTile, nr - m0));
+                return true;
+            }
+            nchunk = 0;
+            while (ok) {
+                if (entered) next_task();
+                entered = true;
+                if (t >= ntask) return false;
+                // the segments of `cur` (loaded a task ago) to shared memory; the
+                // next task's loads go out now
+                store_segs(cur, pre);
+                load_segs(nx1, pre);
+                kp = int(cur.kpad);
+                nr = int(cur.rows);
+                if (nr <= 0) continue;
+                if (kp <= 0) {
+                    if (!accumulate) post(cur.dst * nrhs + c0, 0, nr);
+                    continue;
+                }
+                nchunk = (kp + KC - 1) / KC;
+                Am = ops + cur.aoff;
+                nseg = cur.nseg <= P::kSegCap ? int(cur.nseg) : -1;
+                m0 = 0;
+                post(cur.dst * nrhs + c0, nchunk, min(tc::kRowsTile, nr));
+                return true;
+            }
+            return false;
+        };
+        // coefficient row of K entry k (-1: none): the segment with col <= k < col + len
+        // (k grows along a row tile, so the segment index `h` of a lane only moves forward)
+        int hint[(KC + 31) / 32];
+        auto source = [&](int k, int& h) -> int64_t {
+            if (k >= kp) return -1;
+            if (nseg >= 0) {
+                while (h < nseg && wcol[h] + wlen[h] <= k) ++h;
+                return (h < nseg && wcol[h] <= k) ? woff[h] + (k - wcol[h]) : -1;
+            }
+            int64_t lo = cur.e0, hi = cur.e0 + cur.nseg;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (seg_col[mid] <= k) lo = mid + 1; else hi = mid;
+            }
+            return (lo > cur.e0 && k < seg_col[lo - 1] + seg_len[lo - 1])
+                       ? seg_off[lo - 1] + (k - seg_col[lo - 1]) : -1;
+        };
+        uint32_t g = 0;             // chunks issued
+        // issue chunk g into stage g % NS: table, cp.async of its A units and
+        // coefficient rows (zero-filled where there is no source)
+        auto issue = [&]() -> bool {
+            const int st = int(g % NS);
+            int go_on = 1;
+            if (lane == 0) {
+                if (g >= NS && !tc::mbar_wait(&empty[st], ((g / NS) - 1) & 1, tc::kWaitLimit)) on_fail();
+                go_on = !*fail;
+            }
+            if (!__shfl_sync(0xffffffffu, go_on, 0)) return false;
+            if (lane != 0 && g >= NS) tc::mbar_wait(&empty[st], ((g / NS) - 1) & 1, tc::kWaitLimit);
+#pragma unroll
+            for (int j = 0; j < (KC + 31) / 32; ++j) {
+                const int e = lane + 32 * j;
+                if (e < KC) {
+                    if (ch == 0) hint[j] = 0;
+                    wtab[e] = source(ch * KC + e, hint[j]);
+                }
+            }
+            __syncwarp();
+            uint8_t* At = smem + st * P::kStage;
+            float* raw = reinterpret_cast<float*>(At + (SPLIT ? 2 : 1) * (P::kATile + P::kBTile));
+            const int mt = min(tc::kRowsTile, nr - m0);
             const int k0 = ch * KC;
 #pragma unroll
-            for (int i = 0; i < kAPer; ++i) {
-                const int u = tid + i * tc::kThreads;
-                const int r = (u >> 7) * 8 + (u & 7), q = (u >> 3) & 15;
-                const int kk = k0 + q * (8 / ES);
-                av[i] = make_uint2(0u, 0u);
-                if (r < mt && kk < kp)
-                    av[i] = __ldg(reinterpret_cast<const uint2*>(Am + int64_t(m0 + r) * kp + kk));
-            }
-            const int64_t* src = tab + slot * KC;
-#pragma unroll
-            for (int i = 0; i < kBPer; ++i) {
-                const int v = tid + i * tc::kThreads;
-                const int c = ((v >> 5) % (NT / 8)) * 8 + (v & 7);
-                const int kb = ((v >> 5) / (NT / 8)) * (4 * KPW) + ((v >> 3) & 3) * KPW;
-#pragma unroll
-                for (int j = 0; j < KPW; ++j) {
-                    const int64_t si = src[kb + j];
-                    bv[i][j] = (si >= 0 && c < ncols) ? vec[si * nrhs + c0 + c] : 0.0f;
-                }
-            }
-        };
-        for (int m0 = 0; m0 < nr && ok && nchunk > 0; m0 += tc::kRowsTile) {
-            const int mt = min(tc::kRowsTile, nr - m0);  // rows of this tile
-            // prologue: chunk 0's table and loads
-            build_table(0, int(g & 1));
-            __syncthreads();
-            load_chunk(m0, mt, 0, int(g & 1));
-            for (int ch = 0; ch < nchunk; ++ch, ++g) {
-                const int b = int(g & 1);
-                uint8_t* At = smem + b * kBufBytes;
-                uint8_t* Bt = At + tc::kATileBytes;
-                if (ch + 1 < nchunk) build_table(ch + 1, b ^ 1);
-                if (g >= 2) {                            // MMAs of chunk g - 2 read this buffer
-                    if (tid == 0 && !tc::mbar_wait(&bar[b], ((g - 2) >> 1) & 1, tc::kWaitLimit)) *fail = 1;
-                }
-                __syncthreads();
-                if (*fail) { ok = false; break; }
-#pragma unroll
-                for (int i = 0; i < kAPer; ++i) {
-                    const int u = tid + i * tc::kThreads;
-                    const int r = (u >> 7) * 8 + (u & 7), q = (u >> 3) & 15;
-                    if (r < mt) *reinterpret_cast<uint2*>(At + tc::tile_off(r, q * 8)) = av[i];
-                }
-#pragma unroll
-                for (int i = 0; i < kBPer; ++i) {
-                    const int v = tid + i * tc::kThreads;
-                    const int c = ((v >> 5) % (NT / 8)) * 8 + (v & 7);
-                    const int kb = ((v >> 5) / (NT / 8)) * (4 * KPW) + ((v >> 3) & 3) * KPW;
-                    *reinterpret_cast<uint32_t*>(Bt + tc::tile_off(c, kb * ES)) = In::pack(bv[i]);
-                }
-                // the next chunk's loads fly during the barrier and the MMA issue
-                if (ch + 1 < nchunk) load_chunk(m0, mt, ch + 1, b ^ 1);
-                tc::fence_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::tc_fence_after();
-                    const uint32_t a0 = tc::smem_u32(At), b0 = tc::smem_u32(Bt);
-#pragma unroll
-                    for (int s = 0; s < tc::kChunkBytes / 32; ++s) {   // K = 32 bytes per MMA
-                        const uint64_t ad = tc::smem_desc(a0 + s * 256, 128, 1024);
-                        const uint64_t bd = tc::smem_desc(b0 + s * 256, 128, 1024);
-                        tc::mma<In::BF>(tmem, ad, bd, kIdesc, (ch > 0 || s > 0) ? 1u : 0u);
+            for (int i = 0; i < AUNITS; ++i) {
+                // a warp step covers 8 rows x 4 units (16 bytes fp32, 8 bytes
+                // bf16); SPG steps cover a row group
+                const int r = (pw * AUNITS + i) / SPG * 8 + (lane & 7);
+                const int q = ((pw * AUNITS + i) % SPG) * 4 + (lane >> 3);
+                if (r < mt) {
+                    const int kk = k0 + q * 4;              // 4 entries per unit
+                    const S* rowp = Am + int64_t(m0 + r) * kp;
+                    if constexpr (SPLIT) {
+                        const int bytes = max(0, min(16, (kp - kk) * 4));
+                        tc::cp_async16(At + tc::ctile_off(r, q * 16), rowp + (bytes > 0 ? kk : 0), bytes);
+                    } else {
+                        const int bytes = max(0, min(8, (kp - kk) * 2));
+                        tc::cp_async8(At + tc::ctile_off(r, q * 8), rowp + (bytes > 0 ? kk : 0), bytes);
                     }
-                    tc::mma_commit(&bar[b]);
                 }
             }
-            if (!ok) break;
-            // all MMAs of this row tile complete (the last commit covers earlier ones)
-            if (tid == 0 && g > 0 && !tc::mbar_wait(&bar[(g - 1) & 1], ((g - 1) >> 1) & 1, tc::kWaitLimit))
-                *fail = 1;
-            __syncthreads();
-            if (*fail) { ok = false; break; }
+#pragma unroll
+            for (int i = 0; i < RUNITS; ++i) {
+                const int u = ptid + tc::kProducerThreads * i;
+                if (RTOTAL % tc::kProducerThreads != 0 && u >= RTOTAL) break;
+                const int k = u / (NT / 4), n = 4 * (u % (NT / 4));
+                const int64_t si = wtab[k];
+                float* d = raw + k * P::kRawLd + n;
+                const float* src = vec + (si >= 0 ? si : 0) * nrhs + c0 + n;
+                if (raw16) {
+                    const int bytes = si >= 0 ? max(0, min(16, (ncols - n) * 4)) : 0;
+                    tc::cp_async16(d, bytes > 0 ? src : vec, bytes);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool has = si >= 0 && n + j < ncols;
+                        tc::cp_async4(d + j, has ? src + j : vec, has ? 4 : 0);
+                    }
+                }
+            }
+            tc::cp_async_arrive(&landed[st]);
+            __syncwarp();                                  // table read before the next chunk's
+            return true;
+        };
+        // publish chunk c (its copies landed): split the fp32 A units into tf32
+        // hi / lo terms, transpose the raw coefficients into the K-major B tile
+        // (hi / lo, or bf16 pairs), then arrive on full[s]
+        auto publish = [&](uint32_t c) -> bool {
+            const int st = int(c % NS);
+            // every producer's copies of this chunk landed (the transpose reads
+            // coefficients other threads copied)
+            if (!tc::mbar_wait(&landed[st], (c / NS) & 1, tc::kWaitLimit)) {
+                on_fail();
+                return false;
+            }
+            uint8_t* At = smem + st * P::kStage;
+            uint8_t* Bt = At + (SPLIT ? 2 : 1) * P::kATile;
+            const float* raw = reinterpret_cast<const float*>(At + (SPLIT ? 2 : 1) * (P::kATile + P::kBTile));
+            if constexpr (SPLIT) {
+                uint8_t* Alo = At + P::kATile;
+#pragma unroll
+                for (int i = 0; i < AUNITS; ++i) {
+                    const int r = (pw * AUNITS + i) / SPG * 8 + (lane & 7);
+                    const int q = ((pw * AUNITS + i) % SPG) * 4 + (lane >> 3);
+                    const uint32_t off = tc::ctile_off(r, q * 16);
+                    float4 x = *reinterpret_cast<const float4*>(At + off), h, l;
+                    tc::split_tf32(x.x, h.x, l.x);
+                    tc::split_tf32(x.y, h.y, l.y);
+                    tc::split_tf32(x.z, h.z, l.z);
+                    tc::split_tf32(x.w, h.w, l.w);
+                    *reinterpret_cast<float4*>(At + off) = h;
+                    *reinterpret_cast<float4*>(Alo + off) = l;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < BWORDS; ++i) {
+                const int combo = pw + 4 * i;
+                const int n = (combo % (NT / 8)) * 8 + (lane & 7);
+                const int kw = (combo / (NT / 8)) * 4 + (lane >> 3);
+                const uint32_t off = tc::ctile_off(n, kw * 4);
+                if constexpr (SPLIT) {
+                    float h, l;
+                    tc::split_tf32(raw[kw * P::kRawLd + n], h, l);
+                    *reinterpret_cast<float*>(Bt + off) = h;
+                    *reinterpret_cast<float*>(Bt + P::kBTile + off) = l;
+                } else {
+                    const __nv_bfloat162 v =
+                        __floats2bfloat162_rn(raw[(2 * kw) * P::kRawLd + n], raw[(2 * kw + 1) * P::kRawLd + n]);
+                    *reinterpret_cast<uint32_t*>(Bt + off) = *reinterpret_cast<const uint32_t*>(&v);
+                }
+            }
+            tc::fence_async_smem();
+            tc::mbar_arrive(&full[st]);
+            return true;
+        };
+        // chunks g - kLag + 1 .. g stay in flight while chunk g - kLag is published
+        uint32_t pub = 0;
+        bool go = advance();
+        while (go) {
+            if (!issue()) break;
+            ++g;
+            if (g - pub > uint32_t(P::kLag) && !publish(pub++)) break;
+            go = advance();
+        }
+        if (!go && ok) {
+            while (pub < g && publish(pub)) ++pub;
+            post(0, -1, 0);                                // end of the sequence
+        }
+        tc::cp_async_wait_all();
+    } else if (warp == tc::kMmaWarp) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            uint32_t e = 0, g = 0, ti = 0;
+            for (;;) {
+                const int slot = int(e % RING);
+                if (!tc::mbar_wait(&info[slot], (e / RING) & 1, tc::kWaitLimit)) {
+                    on_fail();
+                    break;
+                }
+                const int nchunk = int(ring[slot * 2 + 1] >> 32);
+                tc::mbar_arrive(&info_free[slot]);
+                ++e;
+                if (nchunk < 0) break;
+                if (nchunk == 0) continue;                 // zero-filled by the epilogue
+                const uint32_t a = ti & 1;
+                if (ti >= 2 && !tc::mbar_wait(&acc_empty[a], ((ti >> 1) - 1) & 1, tc::kWaitLimit)) {
+                    on_fail();
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t d = tmem + a * NT;
+                bool ok = true;
+                for (int ch = 0; ch < nchunk; ++ch, ++g) {
+                    const int st = int(g % NS);
+                    if (!tc::mbar_wait(&full[st], (g / NS) & 1, tc::kWaitLimit)) {
+                        on_fail();
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(smem + st * P::kStage);
+                    const uint32_t b0 = a0 + (SPLIT ? 2 : 1) * P::kATile;
+#pragma unroll
+                    for (int s = 0; s < CB / 32; ++s) {            // K = 32 bytes per MMA
+                        const uint64_t ad = tc::smem_desc(a0 + s * 256, 128, 8 * CB);
+                        const uint64_t bd = tc::smem_desc(b0 + s * 256, 128, 8 * CB);
+                        tc::mma<!SPLIT>(d, ad, bd, kIdesc, (ch > 0 || s > 0) ? 1u : 0u);
+                        if constexpr (SPLIT) {
+                            const uint64_t adl = tc::smem_desc(a0 + P::kATile + s * 256, 128, 8 * CB);
+                            const uint64_t bdl = tc::smem_desc(b0 + P::kBTile + s * 256, 128, 8 * CB);
+                            tc::mma<false>(d, ad, bdl, kIdesc, 1u);
+                            tc::mma<false>(d, adl, bd, kIdesc, 1u);
+                        }
+                    }
+                    tc::mma_commit(&empty[st]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&acc_full[a]);
+                ++ti;
+            }
+            // every MMA of this CTA complete before the TMEM is released
+            if (g > 0) {
+                const uint32_t last = g - 1;
+                tc::mbar_wait(&empty[last % NS], (last / NS) & 1, tc::kWaitLimit);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3, etid = tid - 32 * tc::kProducerWarps;
+        const bool vec4 = (nrhs % 4 == 0) && (c0 % 4 == 0) && ncols == NT;
+        uint32_t e = 0, ti = 0;
+        for (;;) {
+            const int slot = int(e % RING);
+            if (!tc::mbar_wait(&info[slot], (e / RING) & 1, tc::kWaitLimit)) {
+                on_fail();
+                break;
+            }
+            const int64_t yoff = ring[slot * 2];
+            const int64_t w = ring[slot * 2 + 1];
+            tc::mbar_arrive(&info_free[slot]);
+            ++e;
+            const int nchunk = int(w >> 32), nrow = int(uint32_t(w));
+            if (nchunk < 0) break;
+            float* y = vec + yoff;
+            if (nchunk == 0) {                             // a task without columns: y = 0
+                for (int j = etid; j < nrow * ncols; j += tc::kEpiThreads)
+                    y[int64_t(j / ncols) * nrhs + (j % ncols)] = 0.0f;
+                continue;
+            }
+            const uint32_t a = ti & 1;
+            if (!tc::mbar_wait(&acc_full[a], (ti >> 1) & 1, tc::kWaitLimit)) {
+                on_fail();
+                break;
+            }
+            ++ti;
             tc::tc_fence_after();
-            const int quarter = warp & 3, half = warp >> 2;
-            const int row = m0 + quarter * 32 + lane;
-            const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16);
+            const int row = quarter * 32 + lane;
+            const uint32_t tb = tmem + (uint32_t(quarter * 32) << 16) + a * NT;
+            uint32_t v[NT];
 #pragma unroll
-            for (int c8 = half * (NT / 2); c8 < (half + 1) * (NT / 2); c8 += 8) {
-                float v[8];
-                tc::tmem_ld8(tbase + uint32_t(c8), v);
-                if (row < nr) {
-                    float* yo = y + int64_t(row) * nrhs + c8;
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (c8 + k < ncols) yo[k] = accumulate ? yo[k] + v[k] : v[k];
-                }
-            }
+            for (int c8 = 0; c8 < NT; c8 += 8)
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                    : "=r"(v[c8]), "=r"(v[c8 + 1]), "=r"(v[c8 + 2]), "=r"(v[c8 + 3]), "=r"(v[c8 + 4]),
+                      "=r"(v[c8 + 5]), "=r"(v[c8 + 6]), "=r"(v[c8 + 7])
+                    : "r"(tb + uint32_t(c8)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             tc::tc_fence_before();
-            __syncthreads();                             // TMEM reads done before the next tile
-            tc::tc_fence_after();
+            tc::mbar_arrive(&acc_empty[a]);                // accumulator free for tile ti + 2
+            if (row < nrow) {
+                float* yo = y + int64_t(row) * nrhs;
+                if (vec4) {
+#pragma unroll
+                    for (int c = 0; c < NT; c += 4) {
+                        float4 o = make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]),
+                                               __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
+                        if (accumulate) {
+                            const float4 p = *reinterpret_cast<const float4*>(yo + c);
+                            o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
+                        }
+                        *reinterpret_cast<float4*>(yo + c) = o;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NT; ++c)
+                        if (c < ncols) yo[c] = accumulate ? yo[c] + __uint_as_float(v[c]) : __uint_as_float(v[c]);
+                }
+            }
         }
     }
-    if (!ok) {
-        // bounded wait for the MMAs still in flight before the TMEM is released
-        if (tid == 0) {
-            atomicExch(err, tc::kErrTimeout);
-            if (g > 0) tc::mbar_wait(&bar[(g - 1) & 1], ((g - 1) >> 1) & 1, tc::kWaitLimit);
-        }
-        __syncthreads();
-    }
-    if (warp == 0) {
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == tc::kMmaWarp) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, kCols);
+        tc::tmem_dealloc(tmem, P::kCols);
     }
 }
 

@@ -1,15 +1,22 @@
-"""Tensor-core products (tcgen05): bfloat16 storage and fp32 storage with
-tf32 tensor cores, through the C ABI.
+"""Tensor-core products (tcgen05): bfloat16 storage and fp32 storage on the
+tensor cores, through the C ABI.
 
 Bars follow the fp32 parity bar of test_gpu_parity.py, |y_i - ref_i| <=
-64 u (|K||q|)_i, with u the unit roundoff of the format that limits the
-product: u = 2^-8 for bfloat16 operators (8-bit significand) and u = 2^-11
-for tf32 multiplies (11-bit significand).  The reference is the oracle's own
-construction and MVP in fp64 (same pivots, so the difference is rounding
-only).  A tensor-core product rounds the coefficients of every stage to the
-MMA input format as well as the operators, so it is also compared with the
-CUDA-core product of the same handle (fp32 coefficients) under 2 x the bar,
-and its own bar against the oracle is 2 x (both operands rounded).
+64 u (|K||q|)_i, with u the relative rounding of one product in the format
+that limits it: u = 2^-8 for bfloat16 operators (8-bit significand) and
+u = 2^-20 for fp32 operators on the 3-term tf32 product (a = a_hi + a_lo,
+b = b_hi + b_lo with tf32 hi terms; the dropped a_lo b_lo and the tf32
+rounding of the lo terms leave ~2^-21 per product).  The reference is the
+oracle's own construction and MVP in fp64 (same pivots, so the difference is
+rounding only).  A bf16 tensor-core product rounds the coefficients of every
+stage to bf16 as well as the operators, so its bar against the oracle is 2 x
+and it is also compared with the CUDA-core product of the same handle.
+
+bf16 operators leave the 2D log r products of these tolerances without a
+correct digit (the nested pivot bases carry entries that cancel, with
+condition ~1/eps, and log r sums cancel ~20x): bf16 is an inner operator for
+iterative refinement there (test_bf16_refinement_reaches_the_fp64_tolerance),
+and its relative-error bar applies to 3D 1/r only.
 """
 
 import numpy as np
@@ -53,20 +60,23 @@ def test_bf16_storage_matches_the_oracle(kind, d):
           f"RE vs oracle {re:.2e}")
     assert np.all(np.isfinite(Y))
     assert r_tc <= 1.0 and r_cc <= 1.0 and r_x <= 1.0
+    if kind == "invr":
+        assert re <= 1e-2
 
 
 @pytest.mark.parametrize("nrhs", [64, 40, 16, 21])
 def test_fp32_tensor_cores_match_the_oracle(nrhs):
-    """tf32 tiles of 64 / 32 / 16 columns plus CUDA-core remainders."""
+    """3-term tf32 tiles of 64 / 32 / 16 columns plus CUDA-core remainders."""
     N = 5000
     P, Q, ref, absKq = _case("log2d", 2, N, nrhs, 41)
     A = H2Matrix(P, "log2d", leaf_size=64, tol=1e-8, storage="f32", near="stored",
                  tensor_cores=True)
     Y = A.matvec(_dev(Q)).cpu().numpy().reshape(N, nrhs)
-    r = _ratio(Y, ref, 64 * 2.0 ** -11 * absKq)
+    r = _ratio(Y, ref, 64 * 2.0 ** -20 * absKq)
     re = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
-    print(f"tf32 nrhs {nrhs}: {r:.3f} of the bar; RE vs oracle {re:.2e}")
+    print(f"tf32x3 nrhs {nrhs}: {r:.3f} of the bar; RE vs oracle {re:.2e}")
     assert r <= 1.0
+    assert re <= 1e-4
     # columns beyond the tensor-core tiles run on the CUDA cores in fp32
     tc_cols = 64 * (nrhs // 64) + 32 * ((nrhs % 64) // 32) + 16 * ((nrhs % 32) // 16)
     if tc_cols < nrhs:
@@ -102,3 +112,24 @@ def test_bf16_c3_sampled_rows_against_the_exact_product():
     re = np.linalg.norm(Y[idx] - exact) / np.linalg.norm(exact)
     print(f"c3 bf16: {r:.3f} of the bar; RE on sampled rows {re:.2e}")
     assert r <= 1.0
+
+
+def test_fp32_tensor_cores_c3_sampled_rows_against_the_exact_product():
+    """The 64-RHS workload (2D log r, N = 2^20, eps 1e-10) with fp32 operators on
+    the tensor cores (3-term tf32): 8 sampled rows x 64 RHS against the exact
+    product (the oracle's dense rows), under the bar of the 3-term product.
+    Storing the operators of eps = 1e-10 in fp32 (pivot matrices with condition
+    ~1/eps) limits any fp32 product to a few 1e-4 here; the relative error must
+    stay below 1e-3."""
+    w = inputs.workload("c3_2d_log_n1048576")
+    P, Q = w["points"], w["q"].reshape(w["N"], 64)
+    A = H2Matrix(P, "log2d", leaf_size=64, tol=1e-10, storage="f32", near="stored",
+                 tensor_cores=True)
+    Y = A.matvec(_dev(Q)).cpu().numpy()
+    idx = np.random.default_rng(7).choice(w["N"], 8, replace=False)
+    exact = dense.rows("log2d", P, Q, idx)
+    absrow = np.abs(kernels.block("log2d", P, idx, np.arange(w["N"]))) @ np.abs(Q)
+    r = _ratio(Y[idx], exact, 64 * 2.0 ** -20 * absrow)
+    re = np.linalg.norm(Y[idx] - exact) / np.linalg.norm(exact)
+    print(f"c3 tf32x3: {r:.3f} of the bar; RE on sampled rows {re:.2e}")
+    assert r <= 1.0 and re <= 1e-3
