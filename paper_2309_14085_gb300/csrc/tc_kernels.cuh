@@ -13,8 +13,8 @@
 // 2^-11; bf16 operators run as one bf16 product.
 //
 // Shared-memory tiles use the canonical no-swizzle K-major layout: 8-row x
-// 16-byte core matrices, 128 B apart along K (leading byte offset) and 1024 B
-// apart along M / N (stride byte offset).  Every mbarrier wait is bounded: on
+// 16-byte core matrices, 128 B apart along K (leading byte offset) and 8 kCB
+// bytes apart along M / N (stride byte offset).  Every mbarrier wait is bounded: on
 // expiry the CTA records an error code in *err, waits (bounded) for its MMAs in
 // flight, frees its TMEM and returns.
 #pragma once

@@ -345,12 +345,37 @@ def test_error_falls_with_tolerance_and_matches_paper_order():
         H = h2.H2(P, "log2d", n_max=32, eps=eps)
         errs.append(dense.relative_error(H.matvec(q), ex))
     assert all(b < a for a, b in zip(errs, errs[1:]))
-    # the paper's H2*(b+t) rows have RE_MVP / eps between 0.8 and 115
-    ratios = [float(r[3]) / float(r[1]) for r in _golden("paper_re_mvp.txt")]
+    # the paper's H2*(b+t) rows at the smallest N of each table (102400 in 2D,
+    # 64000 in 3D) have RE_MVP / eps between 0.8 and 7.7; within a factor 3 of that
+    rows = _golden("paper_re_mvp.txt")
+    nmin = {d: min(int(r[2]) for r in rows if r[0] == d) for d in ("2", "3")}
+    ratios = [float(r[3]) / float(r[1]) for r in rows if int(r[2]) == nmin[r[0]]]
     lo, hi = min(ratios), max(ratios)
-    assert 0.5 < lo and hi < 150
+    assert 0.7 < lo and hi < 8
     for e, eps in zip(errs, (1e-4, 1e-6, 1e-8, 1e-10, 1e-12)):
-        assert 0.1 * lo <= e / eps <= 2 * hi
+        assert lo / 3 <= e / eps <= 3 * hi
+
+
+def test_oracle_accuracy_at_the_papers_mvp_configurations():
+    """RE_MVP of the oracle's H2*(b+t) at two configurations of the paper's MVP
+    tables, as written by tests/golden/make_paper_configs.py (oracle only),
+    against the values the paper prints (§6.1.1, §6.2.1).  3D 1/r, n_max 125,
+    N = 64000, eps 1e-6: within a factor 3 of the paper's 1.69e-6.  2D log r,
+    n_max 100, N = 102400, eps 1e-8: the paper prints 1.82e-8 and the oracle
+    reaches 2.2e-7; no reading of the ACA stopping rule tried closes that gap
+    (they are listed with their errors in the design notes), so this bound only
+    guards against the error growing further."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "oracle_re_paper_configs.txt"))
+            if l.strip() and not l.startswith("#")]
+    got = {(int(r[0]), int(r[2])): (float(r[6]), float(r[7])) for r in rows}
+    paper = {(int(r[0]), int(r[2])): float(r[3]) for r in _golden("paper_re_mvp.txt")
+             if (r[0], r[1]) in (("2", "1e-8"), ("3", "1e-6"))}
+    re3, p3 = got[(3, 64000)]
+    assert p3 == paper[(3, 64000)]
+    assert p3 / 3 <= re3 <= 3 * p3
+    re2, p2 = got[(2, 102400)]
+    assert p2 == paper[(2, 102400)]
+    assert re2 <= 15 * p2
 
 
 def test_h2sqrt_near_field_is_larger():
