@@ -50,38 +50,132 @@ def _peaks():
 
 
 # ----------------------------------------------------------------------------- oracle legs
-def oracle_rows_child(workload, seconds):
-    """Runs in a fresh single-threaded process: exact rows of K q by the oracle."""
+#: points of the sample on which the oracle's own H2* MVP is timed (its
+#: construction, once per geometry, is not timed; at N = 8192 it takes ~10 s)
+MVP_SAMPLE_N = 8192
+
+
+def oracle_child(kind, workload, seconds):
+    """Runs in a fresh single-threaded process.  kind 'rows': exact rows of
+    K q by the oracle's dense definition (O1), sampled until `seconds` of
+    work; kind 'mvp': the oracle's H2*(b+t) MVP (O2) on MVP_SAMPLE_N points of
+    the same kernel, tolerance and leaf size, repeated until `seconds`."""
+    from oracle import dense, h2
+    from paper_2309_14085_gb300 import inputs
+    w = inputs.workload(workload)
+    nrhs = w["nrhs"]
+    if kind == "rows":
+        P, q = w["points"], w["q"]
+        rng = np.random.default_rng(0)
+        rows, t_used = 0, 0.0
+        while t_used < seconds:
+            idx = rng.choice(P.shape[0], 16, replace=False)
+            t0 = time.perf_counter()
+            dense.rows(w["kernel"], P, q, idx, chunk=16)
+            t_used += time.perf_counter() - t0
+            rows += 16
+        out = {"units": rows, "seconds": t_used, "value": rows * nrhs / t_used}
+    else:
+        n = min(w["N"], MVP_SAMPLE_N)
+        P = inputs.points(n, w["d"], 1000 + w["number"])
+        q = inputs.rhs(n, nrhs, 2000 + w["number"])
+        H = h2.H2(P, w["kernel"], n_max=w["n_max"], eps=w["eps"])
+        done, t_used = 0, 0.0
+        while t_used < seconds or done == 0:
+            t0 = time.perf_counter()
+            H.matvec(q)
+            t_used += time.perf_counter() - t0
+            done += 1
+        out = {"units": done * n, "seconds": t_used, "value": done * n * nrhs / t_used, "n": n}
+    print(json.dumps(out))
+
+
+def reference_child(workload, rows, warmup, steps):
+    """Runs in a fresh single-threaded process: warmup + steps exact products
+    on `rows` sampled rows each; prints the time of every timed step."""
     from oracle import dense
     from paper_2309_14085_gb300 import inputs
     w = inputs.workload(workload)
     P, q = w["points"], w["q"]
     rng = np.random.default_rng(0)
-    rows, t_used = 0, 0.0
-    chunk = 16
-    while t_used < seconds:
-        idx = rng.choice(P.shape[0], chunk, replace=False)
+    ms = []
+    for i in range(warmup + steps):
+        idx = rng.choice(P.shape[0], rows, replace=False)
         t0 = time.perf_counter()
-        dense.rows(w["kernel"], P, q, idx, chunk=chunk)
-        t_used += time.perf_counter() - t0
-        rows += chunk
-    nrhs = w["nrhs"]
-    print(json.dumps({"rows": rows, "seconds": t_used, "value": rows * nrhs / t_used}))
+        dense.rows(w["kernel"], P, q, idx, chunk=16)
+        if i >= warmup:
+            ms.append(1e3 * (time.perf_counter() - t0))
+    print(json.dumps({"step_ms": ms}))
 
 
-def run_oracle_rows(workload, seconds):
+def run_oracle(kind, workload, seconds, procs=1):
+    """The oracle leg `kind` in `procs` single-threaded processes at once (one
+    independent replica per host core); value = the sum of their rates."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", workload,
-                        str(seconds)], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
-                       env=env, timeout=600)
-    if p.returncode != 0:
-        raise RuntimeError("oracle child failed: " + p.stderr[-2000:])
-    r = json.loads(p.stdout.strip().splitlines()[-1])
-    r["cores"] = 1
-    r["sample"] = (f"{r['rows']} exact rows of K q (dense definition, oracle.dense.rows) of "
-                   f"the same workload, {r['seconds']:.1f} s single-threaded")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", kind, workload, str(seconds)]
+    ps = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+          for _ in range(procs)]
+    res = []
+    for p in ps:
+        out, err = p.communicate(timeout=900)
+        if p.returncode != 0:
+            raise RuntimeError("oracle child failed: " + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    r = {"value": float(sum(x["value"] for x in res)), "cores": procs,
+         "seconds": max(x["seconds"] for x in res)}
+    if kind == "rows":
+        r["sample"] = (f"{sum(x['units'] for x in res)} exact rows of K q (dense definition, "
+                       f"oracle.dense.rows) of the same workload, {r['seconds']:.1f} s in {procs} "
+                       f"single-threaded process(es)")
+    else:
+        r["sample"] = (f"oracle H2*(b+t) MVP (oracle.h2, construction not timed) on N = "
+                       f"{res[0]['n']} points of the same kernel, eps and leaf size, "
+                       f"{r['seconds']:.1f} s in {procs} single-threaded process(es)")
     return r
+
+
+def cpu_baselines(workload, seconds):
+    """The oracle on the host: its H2* MVP (O2) and its exact rows (O1), each on
+    one core and on every core (os.cpu_count() processes)."""
+    nproc = os.cpu_count() or 1
+    legs = {}
+    for kind in ("mvp", "rows"):
+        for procs in (1, nproc):
+            legs[f"{kind}_{'1core' if procs == 1 else 'all_cores'}"] = run_oracle(kind, workload, seconds,
+                                                                                procs)
+    main = legs["mvp_all_cores"]
+    return {"value": main["value"], "unit": UNIT, "cores": main["cores"], "kind": "oracle",
+            "sample": main["sample"], "nproc": nproc,
+            "legs": {k: {"value": v["value"], "cores": v["cores"], "sample": v["sample"]}
+                     for k, v in legs.items()}}
+
+
+# ----------------------------------------------------------------------------- accuracy
+GOLDEN = {"c2_3d_invr_n262144": "c2_3d_invr_n262144_rows.txt",
+          "c3_2d_log_n1048576": "c3_2d_log_n1048576_rows.txt"}
+
+
+def golden_accuracy(workload, Y):
+    """Relative 2-norm error of the product Y (N x nrhs, on the device) on the
+    sampled rows whose exact values an oracle-only script wrote under
+    tests/golden/ (the C2 file: row, oracle K~ q, exact K q; the C3 file: row,
+    exact (K Q)[row, :])."""
+    name = GOLDEN.get(workload)
+    if name is None:
+        return None
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None
+    t = np.loadtxt(path, comments="#", ndmin=2)
+    rows = t[:, 0].astype(np.int64)
+    exact = t[:, 2:3] if workload.startswith("c2") else t[:, 1:]
+    import torch
+    got = Y[torch.as_tensor(rows, device=Y.device)].double().cpu().numpy().reshape(len(rows), -1)
+    got = got[:, :exact.shape[1]]
+    re = float(np.linalg.norm(got - exact) / np.linalg.norm(exact))
+    return {"re_vs_exact": re, "rows": int(len(rows)), "rhs": int(exact.shape[1]),
+            "source": f"tests/golden/{name} (exact rows written by the oracle)"}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -203,6 +297,7 @@ def bench_ours(args, rank, world):
         dist.barrier()
     clk = clocks.stop()
     ms_step, value = replica_throughput(e0.elapsed_time(e1), N * nrhs, args.steps, world, dev)
+    accuracy = golden_accuracy(args.workload, Y)
 
     # the same steps again with CUDA events between the pipeline stages (on the
     # stream the kernels run on): per-stage durations and the launch count
@@ -310,6 +405,8 @@ def bench_ours(args, rank, world):
         "gpu_launches": int(launches),   # kernels of the profiled pass = of the timed region
         "roofline": roof,
     }
+    if accuracy is not None:
+        out["accuracy"] = accuracy
     args._handles = getattr(args, "_handles", {})
     args._handles[args.storage] = A
     return out, w
@@ -550,9 +647,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2_3d_invr_n262144")
     ap.add_argument("--storage", default="f64", choices=["f64", "df64", "f32", "bf16"])
-    ap.add_argument("--multi-rhs", default="bf16,tf32",
+    ap.add_argument("--multi-rhs", default="f32,bf16",
                     help="default workload only: also time the 64-RHS workload on the tensor "
-                         "cores in these modes (comma list of bf16, tf32; '' for none)")
+                         "cores in these modes (comma list of f32 (3-term tf32 products of fp32 "
+                         "operators), bf16; '' for none)")
     ap.add_argument("--m2l", default="stored", choices=["stored", "fly", "device"],
                     help="M2L blocks: stored (formed on the host), fly (fp32: evaluated "
                          "from the pivot coordinates in each product), device (stored, "
@@ -565,7 +663,9 @@ def main():
     ap.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS count")
     ap.add_argument("--also", default="df64,f32",
                     help="other storage modes measured in the same run (comma list, '' for none)")
-    ap.add_argument("--oracle-child", nargs=2, default=None)
+    ap.add_argument("--oracle-child", nargs=3, default=None)
+    ap.add_argument("--reference-rows", type=int, default=256,
+                    help="reference arm: exact rows of K q computed by the oracle per step")
     ap.add_argument("--instances", type=int, default=64, help="batched workload: instance count")
     ap.add_argument("--geometries", type=int, default=6, help="served workload: geometries")
     ap.add_argument("--requests", type=int, default=48, help="served workload: requests")
@@ -574,7 +674,11 @@ def main():
     ap.add_argument("--restart", type=int, default=1000, help="served workload: GMRES restart")
     args = ap.parse_args()
     if args.oracle_child:
-        oracle_rows_child(args.oracle_child[0], float(args.oracle_child[1]))
+        kind, wl, arg = args.oracle_child
+        if kind == "steps":
+            reference_child(wl, args.reference_rows, args.warmup, args.steps)
+        else:
+            oracle_child(kind, wl, float(arg))
         return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -591,26 +695,35 @@ def main():
         return
 
     if args.impl == "reference":
+        # the oracle as it stands, on this host: a step is the exact product on a
+        # fixed sample of rows (--reference-rows) of the same workload, one core
         if rank != 0:
             return
         from paper_2309_14085_gb300 import inputs
         w = inputs.workload(args.workload)
-        per_step = max(1.0, min(args.cpu_seconds, 60.0 / max(args.steps + args.warmup, 1)))
-        vals = []
-        r = None
-        for i in range(args.warmup + args.steps):
-            r = run_oracle_rows(args.workload, per_step)
-            if i >= args.warmup:
-                vals.append(r["value"])
-        value = float(np.median(vals))
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", "steps",
+                            args.workload, "0", "--steps", str(args.steps), "--warmup", str(args.warmup),
+                            "--reference-rows", str(args.reference_rows)],
+                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, timeout=1800)
+        if p.returncode != 0:
+            raise RuntimeError("oracle child failed: " + p.stderr[-2000:])
+        r = json.loads(p.stdout.strip().splitlines()[-1])
+        ms = float(np.median(r["step_ms"]))
+        units = args.reference_rows * w["nrhs"]
+        value = units / (ms / 1e3)
+        sample = (f"{args.reference_rows} exact rows of K q per step (oracle.dense.rows, dense "
+                  f"definition) of the same workload, one core; median of {args.steps} steps")
         out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-               "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": 1e3 * w["N"] * w["nrhs"] / value, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic",
                "config": {"workload": args.workload, "N": w["N"], "d": w["d"],
-                          "kernel": KERNEL_NAMES[w["kernel"]], "eps": w["eps"]},
+                          "kernel": KERNEL_NAMES[w["kernel"]], "eps": w["eps"],
+                          "rows_per_step": args.reference_rows},
                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": r["sample"]},
+                                "sample": sample},
                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
@@ -632,6 +745,7 @@ def main():
             args._handles = a2._handles
             r2 = o2["roofline"]
             extra[st] = {"value": o2["value"], "ms_per_step": o2["ms_per_step"],
+                         "accuracy": o2.get("accuracy"),
                          "dominant": r2["kernel"], "frac": r2.get("frac"),
                          "achieved_gbs": r2.get("achieved"), "stage_ms": r2["stage_ms"],
                          "e2e": o2["e2e"]["value"], "clocks": o2["clocks"],
@@ -646,11 +760,18 @@ def main():
             a3 = argparse.Namespace(**vars(args))
             a3.workload, a3.nrhs, a3.steps = "c3_2d_log_n1048576", 0, 20
             a3.storage, a3.tensor_cores = ("bf16", False) if mode == "bf16" else ("f32", True)
+            a3.also = ""
             a3._handles = {}
             try:
                 o3, _ = bench_ours(a3, rank, world)
                 r3 = o3["roofline"]
+                acc = o3.get("accuracy")
                 mr[mode] = {"value": o3["value"], "unit": UNIT, "ms_per_step": o3["ms_per_step"],
+                            "accuracy": acc,
+                            # a product whose sampled rows are off by more than 1 % carries no
+                            # usable digits as an MVP (bf16 operators at eps 1e-10, 2D log r):
+                            # such a mode serves as the inner operator of iterative refinement
+                            "usable_as_mvp": bool(acc is not None and acc["re_vs_exact"] <= 1e-2),
                             "e2e": o3["e2e"]["value"], "dominant": r3["kernel"],
                             "frac": r3.get("frac"), "achieved_gbs": r3.get("achieved"),
                             "stage_ms": r3["stage_ms"], "clocks": o3["clocks"],
@@ -662,9 +783,7 @@ def main():
             a3._handles = {}
         out["multi_rhs_tensor_cores"] = mr
     if rank == 0:
-        cb = run_oracle_rows(args.workload, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],
-                               "kind": "oracle", "sample": cb["sample"]}
+        out["cpu_baseline"] = cpu_baselines(args.workload, args.cpu_seconds)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

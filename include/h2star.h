@@ -348,7 +348,9 @@ int h2_gmres(h2_handle h, h2_handle h_res, double shift, double scale, const dou
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call shares the one array and the call
  * clears what must start at zero, so calls that overlap on the GPU (other
- * streams, other handles, other host threads) race: serialise them.
+ * streams, other handles, other host threads) race: serialise them.  While
+ * the call runs on the host it points the handle's own scratch at the array,
+ * so no other call may use the same handle from another host thread meanwhile.
  * Errors: H2_E_INVALID_ARG (NULL pointers, wrong current device, or a handle
  * whose scratch exceeds 32 MiB -- the message states both sizes),
  * H2_E_NO_DEVICE, H2_E_CUDA.

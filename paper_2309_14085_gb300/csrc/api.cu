@@ -892,20 +892,14 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     if (o.storage != H2_F64 && o.storage != H2_F32 && o.storage != H2_DF64 && o.storage != H2_BF16)
         return fail(H2_E_INVALID_ARG, "unknown storage");
     if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(H2_E_INVALID_ARG, "tensor_cores must be 0 or 1");
-    if (o.tensor_cores && o.storage != H2_F32)
-        return fail(H2_E_INVALID_ARG, "tensor_cores applies to H2_F32 storage (H2_BF16 always uses them)");
     if (o.m2l_mode < 0 || o.m2l_mode > 2) return fail(H2_E_INVALID_ARG, "unknown m2l_mode");
-    if (o.m2l_mode == 1 && o.storage != H2_F32)
-        return fail(H2_E_UNSUPPORTED, "M2L on the fly is built for fp32 storage");
-    if (o.storage == H2_BF16 && o.near_mode == 1)
-        return fail(H2_E_UNSUPPORTED, "bf16 storage evaluates the near field from stored blocks only");
-    if (o.storage == H2_BF16 && variant == H2_PLUS_H_STAR)
-        return fail(H2_E_UNSUPPORTED, "(H2+H)* is built for fp64 and fp32 storage");
     if (o.near_mode < 0 || o.near_mode > 2) return fail(H2_E_INVALID_ARG, "unknown near_mode");
-    if (o.storage == H2_DF64 && o.near_mode == 1)
-        return fail(H2_E_UNSUPPORTED, "df64 storage evaluates the near field from stored blocks only");
-    if (o.storage == H2_DF64 && variant == H2_PLUS_H_STAR)
-        return fail(H2_E_UNSUPPORTED, "(H2+H)* is built for fp64 and fp32 storage");
+    {
+        bool unsupported = false;
+        if (const char* why = h2::combination_error(o.storage, variant, o.near_mode, o.tensor_cores,
+                                                    o.m2l_mode, &unsupported))
+            return fail(unsupported ? H2_E_UNSUPPORTED : H2_E_INVALID_ARG, why);
+    }
     if (o.kappa < 0 || o.kappa > 20) return fail(H2_E_INVALID_ARG, "kappa out of range");
     if (o.eps_far < 0 || o.eps_far >= 1 || o.eps_ver < 0 || o.eps_ver >= 1)
         return fail(H2_E_INVALID_ARG, "eps_far / eps_ver must be in [0, 1)");

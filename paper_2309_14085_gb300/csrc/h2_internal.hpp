@@ -165,6 +165,26 @@ struct Host {
     int64_t lowrank_entries = 0;     // stored (H2+H)* factor entries
 };
 
+// The option combinations the library builds (storage 0 fp64, 1 fp32, 2
+// double-float, 3 bf16; variant 1 = (H2+H)*; near_mode 0 default, 1 on the
+// fly, 2 stored; m2l_mode 0 stored, 1 on the fly, 2 formed on the device).
+// Returns nullptr when supported, else the reason, with *unsupported = true for
+// a combination that is well formed but not built (false: an invalid value).
+// h2_build refuses the same combinations that a loaded checkpoint may not hold.
+inline const char* combination_error(int storage, int variant, int near_mode, int tensor_cores,
+                                     int m2l_mode, bool* unsupported) {
+    *unsupported = false;
+    if (tensor_cores && storage != 1)
+        return "tensor_cores applies to H2_F32 storage (H2_BF16 always uses them)";
+    *unsupported = true;
+    if (m2l_mode == 1 && storage != 1) return "M2L on the fly is built for fp32 storage";
+    if (storage == 3 && near_mode == 1) return "bf16 storage evaluates the near field from stored blocks only";
+    if (storage == 2 && near_mode == 1)
+        return "df64 storage evaluates the near field from stored blocks only";
+    if ((storage == 2 || storage == 3) && variant == 1) return "(H2+H)* is built for fp64 and fp32 storage";
+    return nullptr;
+}
+
 // Construction (build.cpp).  Return "" on success or an error message.
 std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf_size,
                        int kappa_forced, const double* domain_lo, double domain_side,

@@ -345,6 +345,16 @@ std::string validate(const Host& H) {
         H.storage > 3 || H.near_mode < 0 || H.near_mode > 2 || (H.tensor_cores & ~1) ||
         (H.m2l_fly & ~1) || (H.m2l_dev & ~1) || (H.m2l_fly && H.m2l_dev))
         return "options out of range";
+    {
+        bool unsupported = false;
+        if (const char* why = combination_error(H.storage, H.variant, H.near_mode, H.tensor_cores,
+                                                H.m2l_fly ? 1 : H.m2l_dev ? 2 : 0, &unsupported))
+            return std::string("option combination: ") + why;
+        // the packed near field is the one the options select (h2_build and
+        // h2_convert keep them in step)
+        const bool stored = H.near_mode == 2 || (H.near_mode == 0 && H.storage != 1);
+        if (bool(H.packed.near_stored) != stored) return "near-field mode disagrees with the packed near field";
+    }
     if ((t.d != 2 && t.d != 3) || t.kappa < 0 || t.d * t.kappa > 24 || t.N < 1) return "tree shape";
     const int K = t.kappa;
     const int64_t N = t.N, nleaf = t.nboxes(K);
@@ -439,10 +449,10 @@ std::string validate(const Host& H) {
     const size_t nbk = P.lr_k.size();
     for (const auto* a : {&P.lr_x0, &P.lr_mx, &P.lr_y0, &P.lr_my, &P.lr_uoff, &P.lr_voff, &P.lr_toff})
         if (a->size() != nbk) return "low-rank arrays differ in length";
-    if (nbk > 0 || !P.lr_level_ptr.empty()) {
-        if (int64_t(P.lr_level_ptr.size()) != K + 2 || !monotone_from0(P.lr_level_ptr, int64_t(nbk)))
-            return "low-rank level pointers";
-    }
+    // the product reads lr_level_ptr[0 .. kappa + 1] whether or not there are blocks
+    if (int64_t(P.lr_level_ptr.size()) != K + 2 || !monotone_from0(P.lr_level_ptr, int64_t(nbk)))
+        return "low-rank level pointers";
+    if (P.lr_tlen < 0) return "low-rank scratch length";
     for (size_t k = 0; k < nbk; ++k) {
         const int64_t x0 = P.lr_x0[k], mx = P.lr_mx[k], y0 = P.lr_y0[k], my = P.lr_my[k], kk = P.lr_k[k];
         if (x0 < 0 || mx < 0 || x0 + mx > N || y0 < 0 || my < 0 || y0 + my > N || kk < 0)

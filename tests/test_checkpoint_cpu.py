@@ -143,3 +143,80 @@ def test_construction_is_independent_of_the_thread_count(tmp_path):
         A.save(files[-1])
     a, b = (open(f, "rb").read() for f in files)
     assert len(a) == len(b) and a[:60] == b[:60] and a[68:-8] == b[68:-8]
+
+
+def _checksum(b):
+    """The checkpoint's checksum, written out from its definition in the
+    loader's header: little-endian 64-bit words (the last one zero-padded)
+    folded by h <- (h xor w) * P with P the 64-bit FNV prime, from the FNV
+    offset basis, then the byte length folded the same way."""
+    P, M = 0x100000001b3, (1 << 64) - 1
+    h = 0xcbf29ce484222325
+    pad = bytes(b) + b"\0" * ((-len(b)) % 8)
+    for w in np.frombuffer(pad, dtype="<u8").tolist():
+        h = ((h ^ w) * P) & M
+    return ((h ^ len(b)) * P) & M
+
+
+def test_crafted_low_rank_fields_are_rejected(tmp_path):
+    """A file whose checksum is right but whose (H2+H)* level pointers are
+    missing, or whose scratch length is negative, is refused: the product reads
+    lr_level_ptr[0 .. kappa + 1] even when there are no low-rank blocks.  The
+    tail of an H2*(b+t) file is lr_level_ptr (length kappa + 2, all zero),
+    eight empty arrays, lr_tlen and the checksum."""
+    A = _build(CASES[0])
+    f = str(tmp_path / "a.h2")
+    A.save(f)
+    data = open(f, "rb").read()
+    assert _checksum(data[:-8]) == int.from_bytes(data[-8:], "little")    # the definition holds
+    K = A.info()["kappa"]
+    body = data[:-8]
+    tail = 8 + 8 * (K + 2) + 8 * 8 + 8
+    head, old = body[:-tail], body[-tail:]
+    assert int.from_bytes(old[:8], "little") == K + 2 and old[8:] == b"\0" * (tail - 8)
+
+    def load(blob):
+        g = str(tmp_path / "b.h2")
+        open(g, "wb").write(blob + _checksum(blob).to_bytes(8, "little"))
+        return H2Matrix.load(g, host_only=True)
+
+    load(body)                                                  # unchanged: accepted
+    empty_ptr = head + (0).to_bytes(8, "little") + b"\0" * (8 * 8) + (0).to_bytes(8, "little")
+    with pytest.raises(H2Error) as e:
+        load(empty_ptr)
+    assert e.value.code == -1 and "low-rank level pointers" in str(e.value)
+    neg_tlen = body[:-8] + (-1).to_bytes(8, "little", signed=True)
+    with pytest.raises(H2Error) as e:
+        load(neg_tlen)
+    assert e.value.code == -1 and "scratch" in str(e.value)
+
+
+def test_crafted_option_combinations_are_rejected(tmp_path):
+    """Options h2_build refuses are refused in a loaded file too (with a valid
+    checksum), and so is a near-field mode that disagrees with the packed near
+    field: either would make a product skip a stage.  Header bytes (after the
+    8-byte magic): kernel kind 8-11, parameter 12-19, variant 20-23, storage
+    24-27, near mode 28-31, tensor cores 32-35."""
+    A = _build(CASES[0])                          # fp64, stored near field
+    f = str(tmp_path / "a.h2")
+    A.save(f)
+    body = bytearray(open(f, "rb").read()[:-8])
+
+    def load(blob):
+        g = str(tmp_path / "b.h2")
+        open(g, "wb").write(bytes(blob) + _checksum(blob).to_bytes(8, "little"))
+        return H2Matrix.load(g, host_only=True)
+
+    tc = bytearray(body)
+    tc[32:36] = (1).to_bytes(4, "little")         # tensor cores with fp64 storage
+    with pytest.raises(H2Error) as e:
+        load(tc)
+    assert e.value.code == -1 and "combination" in str(e.value)
+    near = bytearray(body)
+    near[28:32] = (1).to_bytes(4, "little")       # "on the fly" over stored blocks
+    with pytest.raises(H2Error) as e:
+        load(near)
+    assert e.value.code == -1 and "near-field mode" in str(e.value)
+    df = bytearray(body)
+    df[24:28] = (2).to_bytes(4, "little")         # double-float, consistent: accepted
+    load(df)

@@ -22,7 +22,7 @@ from paper_2309_14085_gb300 import H2Matrix, inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-F64_TOL = 1e-10
+F64_TOL = 1e-11
 
 
 def _noalloc():
@@ -39,12 +39,17 @@ def _call(f, A, x, y):
              ctypes.c_void_p(s.cuda_stream))
 
 
-@pytest.mark.parametrize("kind,d,N,storage", [("log2d", 2, 4096, "f64"),
-                                              ("invr", 3, 20000, "df64"),
-                                              ("invr", 3, 20000, "f32")])
-def test_noalloc_equals_matvec_on_two_calls(kind, d, N, storage):
+@pytest.mark.parametrize("kind,d,N,storage,variant,m2l", [
+    ("log2d", 2, 4096, "f64", "h2star", None),
+    ("invr", 3, 20000, "df64", "h2star", None),
+    ("invr", 3, 20000, "f32", "h2star", None),
+    ("log2d", 2, 6000, "f64", "h2plush", None),        # the (H2+H)* scratch after the vectors
+    ("invr", 3, 12000, "f32", "h2star", "fly"),        # M2L from the pivot coordinates
+    ("log2d", 2, 6000, "f64", "h2star", "device")])    # M2L blocks formed on the device
+def test_noalloc_equals_matvec_on_two_calls(kind, d, N, storage, variant, m2l):
     L, f = _noalloc()
-    A = H2Matrix(inputs.points(N, d, 500 + d), kind, leaf_size=64, tol=1e-8, storage=storage)
+    A = H2Matrix(inputs.points(N, d, 500 + d), kind, leaf_size=64, tol=1e-8, storage=storage,
+                 variant=variant, m2l=m2l)
     q1 = torch.tensor(inputs.rhs(N, 1, 601), device="cuda:0")
     q2 = torch.tensor(inputs.rhs(N, 1, 602), device="cuda:0")
     for q in (q1, q2):
