@@ -467,7 +467,7 @@ def bench_batched(args):
         # at once and drops its host operators (the batch copies device to device)
         th = max(1, min(ncpu, int(ncpu * i["N"] / 65536.0) or 1))
         m = H2Matrix(i["points"], i["kernel"], leaf_size=64, tol=1e-8, storage=args.storage,
-                     near="stored", threads=th)
+                     near="stored", threads=th, tensor_cores=args.storage == "f32")
         m.release_host()
         return m
 
@@ -498,6 +498,10 @@ def bench_batched(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     pts = info["points_times_rhs"]
+    hbm, how = _peaks()
+    # every instance's operators once per product (the bytes the method must
+    # move at least; the coefficients come on top)
+    ops_gbs = info["bytes_ops"] / (ms / 1e3) / 1e9
     out = {"metric": METRIC, "value": pts / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
@@ -507,8 +511,16 @@ def bench_batched(args):
                       "graph": "one captured CUDA graph per batched product",
                       "host_build_seconds": round(build_s, 1),
                       "device_bytes": info["bytes_device"], "l2": "operators larger than L2"},
-           "clocks": clk, "gpu_launches": info["launches_per_product"] * args.steps}
-    print(json.dumps(out))
+           "clocks": clk, "gpu_launches": info["launches_per_product"] * args.steps,
+           "roofline": {"bound": "hbm", "achieved": round(ops_gbs, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(ops_gbs / hbm, 4), "traffic": None,
+                        "alg_bytes": info["bytes_ops"],
+                        "note": "operator bytes of all instances once per product / product time",
+                        "peak_source": f"{how} hbm_gbs"},
+           "tensor_cores": args.storage == "f32"}
+    if args.standalone:
+        print(json.dumps(out))
+    return out
 
 
 def bench_served(args):
@@ -673,6 +685,7 @@ def main():
     ap.add_argument("--max-active", type=int, default=16, help="served workload: active requests")
     ap.add_argument("--restart", type=int, default=1000, help="served workload: GMRES restart")
     args = ap.parse_args()
+    args.standalone = False
     if args.oracle_child:
         kind, wl, arg = args.oracle_child
         if kind == "steps":
@@ -691,6 +704,7 @@ def main():
     if args.workload == "c4_batched":
         if args.storage == "f64" and "--storage" not in sys.argv:
             args.storage = "f32"
+        args.standalone = True
         bench_batched(args)
         return
 

@@ -55,22 +55,26 @@ struct DevRowTasks {
     int max_rows = 0;             // largest task (rows)
     int64_t *dst = nullptr, *aoff = nullptr, *seg_ptr = nullptr, *seg_off = nullptr;
     int32_t *rows = nullptr, *kpad = nullptr, *seg_len = nullptr, *seg_col = nullptr;
-    // per task, packed for one 48-byte load of the tensor-core kernel:
-    // aoff, dst, first segment, segment count, rows, kpad
+    // per task, packed for one 64-byte load of the tensor-core kernel:
+    // aoff, dst, first segment, segment count, rows, kpad, columns (-1: the
+    // launch's), unused
     int64_t* meta = nullptr;
 };
 
-// the packed task records of DevRowTasks::meta
-std::vector<int64_t> task_meta(const h2::RowTasks& R) {
-    std::vector<int64_t> m(size_t(R.size()) * 6);
+// the packed task records of DevRowTasks::meta; ncols (nullable) gives each
+// task's own RHS column count (the instance's, in a batch)
+std::vector<int64_t> task_meta(const h2::RowTasks& R, const std::vector<int64_t>* ncols = nullptr) {
+    std::vector<int64_t> m(size_t(R.size()) * 8);
     for (int64_t k = 0; k < R.size(); ++k) {
-        int64_t* e = m.data() + k * 6;
+        int64_t* e = m.data() + k * 8;
         e[0] = R.aoff[k];
         e[1] = R.dst[k];
         e[2] = R.seg_ptr[k];
         e[3] = R.seg_ptr[k + 1] - R.seg_ptr[k];
         e[4] = R.rows[k];
         e[5] = R.kpad[k];
+        e[6] = ncols ? (*ncols)[size_t(k)] : -1;
+        e[7] = 0;
     }
     return m;
 }
@@ -340,7 +344,7 @@ template <typename S, int NT> constexpr int tc_smem() { return h2::tc_smem_bytes
 // opt-in maximum, 1 KB reserved per CTA), TMEM (512 columns per SM) and
 // registers (64K per SM).
 template <typename S, int NT>
-int tc_setup_nt(h2_handle h, int nsm, int smem_sm, int slot) {
+int tc_grid(int nsm, int smem_sm, int* blocks, int* occupancy) {
     H2_CUDA(cudaFuncSetAttribute(h2::k_rowgemm_tc<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc_smem<S, NT>()));
     int occ = 0;
@@ -351,9 +355,14 @@ int tc_setup_nt(h2_handle h, int nsm, int smem_sm, int slot) {
     const int by_smem = smem_sm / (tc_smem<S, NT>() + 1024);
     const int by_tmem = 512 / int(h2::tc::Plan<S, NT>::kCols);
     const int by_regs = 65536 / (std::max(fa.numRegs, 1) * h2::tc::kThreadsWs);
-    h->tc_occupancy[slot] = occ;
-    h->tc_blocks[slot] = std::max(1, std::min(std::min(by_smem, by_tmem), by_regs)) * nsm;
+    *occupancy = occ;
+    *blocks = std::max(1, std::min(std::min(by_smem, by_tmem), by_regs)) * nsm;
     return H2_OK;
+}
+
+template <typename S, int NT>
+int tc_setup_nt(h2_handle h, int nsm, int smem_sm, int slot) {
+    return tc_grid<S, NT>(nsm, smem_sm, &h->tc_blocks[slot], &h->tc_occupancy[slot]);
 }
 
 // dynamic shared memory limits and the persistent grid (resident CTAs x SMs)
@@ -1634,6 +1643,13 @@ struct h2_batch_s {
     int storage = 0, ninst = 0, nvirt = 0, device = -1;
     size_t ssize = 8, vsize = 8;
     int nt = 1;                                // RHS columns per virtual instance
+    // fp32 handles built with tensor_cores: every block-row step runs on the
+    // tensor cores in 16-column tiles, so an instance's operators stream once
+    // for all of its (up to 16) columns; per-task column counts bound the reads
+    bool tc = false;
+    int tc_blocks[3] = {0, 0, 0}, tc_occupancy = 0;
+    int* tc_err = nullptr;                     // device flag of an expired wait
+    int* tc_err_host = nullptr;                // pinned copy, read back after each product
     int64_t pts_rhs = 0;                       // sum over instances of N_i nrhs_i
     std::vector<int> inst_of, col_of, ncol;    // per virtual instance
     int32_t* ncol_dev = nullptr;
@@ -1656,6 +1672,7 @@ struct h2_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     ~h2_batch_s() {
+        if (tc_err_host) cudaFreeHost(tc_err_host);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (ev_in) cudaEventDestroy(ev_in);
@@ -1679,7 +1696,8 @@ int bupload(h2_batch b, U** dst, const std::vector<U>& src) {
     return H2_OK;
 }
 
-int bupload_rows(h2_batch b, DevRowTasks& D, const h2::RowTasks& R) {
+int bupload_rows(h2_batch b, DevRowTasks& D, const h2::RowTasks& R,
+                 const std::vector<int64_t>* ncols = nullptr) {
     D.n = R.size();
     H2_TRY(bupload(b, &D.dst, R.dst));
     H2_TRY(bupload(b, &D.aoff, R.aoff));
@@ -1689,7 +1707,7 @@ int bupload_rows(h2_batch b, DevRowTasks& D, const h2::RowTasks& R) {
     H2_TRY(bupload(b, &D.kpad, R.kpad));
     H2_TRY(bupload(b, &D.seg_len, R.seg_len));
     H2_TRY(bupload(b, &D.seg_col, R.seg_col));
-    H2_TRY(bupload(b, &D.meta, task_meta(R)));
+    H2_TRY(bupload(b, &D.meta, task_meta(R, ncols)));
     D.rw = 4;
     D.max_rows = R.rows.empty() ? 0 : *std::max_element(R.rows.begin(), R.rows.end());
     return H2_OK;
@@ -1718,7 +1736,12 @@ int batch_launch_all(h2_batch b, cudaStream_t s) {
     auto rows = [&](const DevRowTasks& R, int acc) {
         if (R.n == 0) return;
         ++b->launches;
-        launch_rows<A>(R, b->ops, b->vec, s, acc, nt, 0, nt);
+        if (b->tc) {
+            if constexpr (std::is_same<A, h2::F32>::value)
+                launch_rows_tc<A>(R, b->ops, b->vec, s, acc, nt, 0, nt, b->tc_err, b->tc_blocks);
+        } else {
+            launch_rows<A>(R, b->ops, b->vec, s, acc, nt, 0, nt);
+        }
     };
     rows(b->p2m, 0);
     for (const auto& R : b->m2m) rows(R, 0);
@@ -1731,6 +1754,7 @@ int batch_launch_all(h2_batch b, cudaStream_t s) {
     ++b->launches;
     k_batch_scatter<<<nblocks(b->total_pts, threads), threads, 0, s>>>(
         b->nvirt, nt, b->pref, b->fb, b->pb, b->ncol_dev, b->perm, b->Ytab, b->vec, b->storage);
+    if (b->tc) H2_CUDA(cudaMemcpyAsync(b->tc_err_host, b->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     return H2_OK;
 }
 
@@ -1774,7 +1798,9 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
     int64_t totN = 0, totV = 0;
     std::vector<int64_t> qoff, voff, pbase(n);
     int64_t pb = 0;
-    B->nt = storage == H2_F32 ? 4 : 2;
+    B->tc = storage == H2_F32;
+    for (int i = 0; i < n; ++i) B->tc = B->tc && hs[i]->host.tensor_cores;
+    B->nt = B->tc ? 16 : storage == H2_F32 ? 4 : 2;
     for (int i = 0; i < n; ++i) {
         pbase[i] = pb;
         pb += hs[i]->host.tree.N;
@@ -1803,6 +1829,12 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
     int kmax = 0;
     for (int i = 0; i < n; ++i) kmax = std::max(kmax, hs[i]->host.tree.kappa);
     std::vector<h2::RowTasks> m2m(std::max(kmax, 1)), l2l(kmax + 1);
+    // per task: its virtual instance's column count (read by the tensor-core path)
+    std::vector<int64_t> p2m_nc, m2l_nc, leaf_nc;
+    std::vector<std::vector<int64_t>> m2m_nc(m2m.size()), l2l_nc(l2l.size());
+    auto cols = [&](std::vector<int64_t>& nc, const h2::RowTasks& R, int v) {
+        nc.resize(size_t(R.size()), int64_t(B->ncol[size_t(v)]));
+    };
     for (int v = 0; v < B->nvirt; ++v) {
         const h2::Host& H = hs[B->inst_of[v]]->host;
         const h2::Packed& P = H.packed;
@@ -1815,11 +1847,20 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
         };
         const int64_t ab = abase[B->inst_of[v]];
         append_rows(p2m, P.p2m, ab, map);
+        cols(p2m_nc, p2m, v);
         append_rows(m2l, P.m2l, ab, map);
+        cols(m2l_nc, m2l, v);
         append_rows(leaf, P.leaf, ab, map);
+        cols(leaf_nc, leaf, v);
         const int K = H.tree.kappa;
-        for (int l = K - 1; l >= 1; --l) append_rows(m2m[K - 1 - l], P.m2m[l], ab, map);   // bottom-up
-        for (int l = 2; l <= K; ++l) append_rows(l2l[l], P.l2l[l], ab, map);              // top-down
+        for (int l = K - 1; l >= 1; --l) {                                                 // bottom-up
+            append_rows(m2m[K - 1 - l], P.m2m[l], ab, map);
+            cols(m2m_nc[size_t(K - 1 - l)], m2m[K - 1 - l], v);
+        }
+        for (int l = 2; l <= K; ++l) {                                                     // top-down
+            append_rows(l2l[l], P.l2l[l], ab, map);
+            cols(l2l_nc[size_t(l)], l2l[l], v);
+        }
     }
     // device data
     {
@@ -1884,18 +1925,30 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
     std::vector<double*> nully(B->nvirt, nullptr);
     H2_TRY(bupload(B.get(), &B->Xtab, nullx));
     H2_TRY(bupload(B.get(), &B->Ytab, nully));
-    H2_TRY(bupload_rows(B.get(), B->p2m, p2m));
-    H2_TRY(bupload_rows(B.get(), B->m2l, m2l));
-    H2_TRY(bupload_rows(B.get(), B->leaf, leaf));
-    for (auto& R : m2m) {
-        if (R.size() == 0) continue;
+    H2_TRY(bupload_rows(B.get(), B->p2m, p2m, &p2m_nc));
+    H2_TRY(bupload_rows(B.get(), B->m2l, m2l, &m2l_nc));
+    H2_TRY(bupload_rows(B.get(), B->leaf, leaf, &leaf_nc));
+    for (size_t k = 0; k < m2m.size(); ++k) {
+        if (m2m[k].size() == 0) continue;
         B->m2m.emplace_back();
-        H2_TRY(bupload_rows(B.get(), B->m2m.back(), R));
+        H2_TRY(bupload_rows(B.get(), B->m2m.back(), m2m[k], &m2m_nc[k]));
     }
-    for (auto& R : l2l) {
-        if (R.size() == 0) continue;
+    for (size_t k = 0; k < l2l.size(); ++k) {
+        if (l2l[k].size() == 0) continue;
         B->l2l.emplace_back();
-        H2_TRY(bupload_rows(B.get(), B->l2l.back(), R));
+        H2_TRY(bupload_rows(B.get(), B->l2l.back(), l2l[k], &l2l_nc[k]));
+    }
+    if (B->tc) {
+        int nsm = 0, smem_sm = 0;
+        H2_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device));
+        H2_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, B->device));
+        H2_TRY((tc_grid<float, 16>(nsm, smem_sm, &B->tc_blocks[2], &B->tc_occupancy)));
+        std::vector<int> zero(1, 0);
+        H2_TRY(bupload(B.get(), &B->tc_err, zero));
+        void* ph = nullptr;
+        H2_CUDA(cudaMallocHost(&ph, sizeof(int)));
+        B->tc_err_host = static_cast<int*>(ph);
+        *B->tc_err_host = 0;
     }
     H2_CUDA(cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking));
     H2_CUDA(cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming));
@@ -1918,6 +1971,9 @@ extern "C" int h2_batch_create(const h2_handle* hs, int n, const int* nrhs, h2_b
 extern "C" int h2_batch_matvec(h2_batch b, const double* const* X, double* const* Y, void* stream) {
     g_err.clear();
     if (!b || !X || !Y) return fail(H2_E_INVALID_ARG, "NULL argument");
+    // the flag of an earlier tensor-core product (read back after each one)
+    if (b->tc_err_host && *b->tc_err_host)
+        return fail(H2_E_TIMEOUT, "a tensor-core product of the batch gave up waiting for its MMAs");
     // per virtual instance: column c of instance i at X[i] + c * N_i (column-major, ld = N_i)
     std::vector<const double*> xt(b->nvirt);
     std::vector<double*> yt(b->nvirt);

@@ -219,7 +219,9 @@ struct Plan {
 //              the operator rows into the stage's canonical no-swizzle K-major
 //              tile (bytes past kpad zero-filled, rows past the task's left
 //              stale: their accumulator rows are never read) and of the
-//              coefficient rows, 16 bytes of the RHS tile at a time, into a raw
+//              coefficient rows (a task's own column count, if its record
+//              gives one, bounds the columns read: the others are zero),
+//              16 bytes of the RHS tile at a time, into a raw
 //              [k][n] tile, each thread then arriving on landed[s] when its
 //              copies land; kLag chunks later (landed[s] complete) the fp32
 //              tiles are split into tf32 hi / lo terms, the coefficients
@@ -315,14 +317,14 @@ __global__ void __launch_bounds__(tc::kThreadsWs, 2) k_rowgemm_tc(
         int64_t* wtab = tab + pw * KC;
         const bool raw16 = (nrhs % 4 == 0) && (c0 % 4 == 0);   // 16-byte aligned coefficient rows
         struct Task {
-            int64_t aoff, dst, e0, nseg, rows, kpad;
+            int64_t aoff, dst, e0, nseg, rows, kpad, ncols;
         };
         auto load_task = [&](int64_t t) -> Task {
-            Task k{0, 0, 0, 0, 0, 0};
+            Task k{0, 0, 0, 0, 0, 0, -1};
             if (t < ntask) {
-                const longlong2* m = reinterpret_cast<const longlong2*>(meta + t * 6);
-                const longlong2 a = __ldg(m), b = __ldg(m + 1), c = __ldg(m + 2);
-                k = Task{a.x, a.y, b.x, b.y, c.x, c.y};
+                const longlong2* m = reinterpret_cast<const longlong2*>(meta + t * 8);
+                const longlong2 a = __ldg(m), b = __ldg(m + 1), c = __ldg(m + 2), e = __ldg(m + 3);
+                k = Task{a.x, a.y, b.x, b.y, c.x, c.y, e.x};
             }
             return k;
         };
@@ -366,6 +368,7 @@ __global__ void __launch_bounds__(tc::kThreadsWs, 2) k_rowgemm_tc(
         Segs pre;
         load_segs(cur, pre);
         int nseg = 0, kp = 0, nr = 0, nchunk = 0, m0 = 0, ch = -1;
+        int tcols = ncols;                  // coefficient columns of the current task
         const S* Am = ops;
         uint32_t posted = 0;                               // ring entries (warp 0)
         bool ok = true;
@@ -421,6 +424,7 @@ __global__ void __launch_bounds__(tc::kThreadsWs, 2) k_rowgemm_tc(
                 }
                 nchunk = (kp + KC - 1) / KC;
                 Am = ops + cur.aoff;
+                tcols = cur.ncols >= 0 ? min(ncols, int(cur.ncols)) : ncols;
                 nseg = cur.nseg <= P::kSegCap ? int(cur.nseg) : -1;
                 m0 = 0;
                 post(cur.dst * nrhs + c0, nchunk, min(tc::kRowsTile, nr));
@@ -497,12 +501,12 @@ __global__ void __launch_bounds__(tc::kThreadsWs, 2) k_rowgemm_tc(
                 float* d = raw + k * P::kRawLd + n;
                 const float* src = vec + (si >= 0 ? si : 0) * nrhs + c0 + n;
                 if (raw16) {
-                    const int bytes = si >= 0 ? max(0, min(16, (ncols - n) * 4)) : 0;
+                    const int bytes = si >= 0 ? max(0, min(16, (tcols - n) * 4)) : 0;
                     tc::cp_async16(d, bytes > 0 ? src : vec, bytes);
                 } else {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const bool has = si >= 0 && n + j < ncols;
+                        const bool has = si >= 0 && n + j < tcols;
                         tc::cp_async4(d + j, has ? src + j : vec, has ? 4 : 0);
                     }
                 }
