@@ -142,6 +142,11 @@ struct h2_handle_s {
     int* tc_err_host = nullptr;
     int tc_blocks[3] = {0, 0, 0};       // persistent grid for RHS tiles of 64 / 32 / 16
     int tc_occupancy[3] = {0, 0, 0};    // cudaOccupancy estimate (reported only)
+    // fp64 storage, near field on the fly, 1/r or the IMQ: the near field runs
+    // in double-float arithmetic on a second stream, beside the far-field steps
+    // (FP32 pipe next to the FP64-pipe-bound M2L), joined before L2P
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -614,6 +619,11 @@ int upload(h2_handle h) {
         h->tc_err_host = static_cast<int*>(ph);
         *h->tc_err_host = 0;
     }
+    if (std::is_same<A, h2::F64>::value && !P.near_stored && (H.kern.kind == 1 || H.kern.kind == 2)) {
+        H2_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        H2_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        H2_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
     H2_CUDA(cudaDeviceSynchronize());
     H2_TRY(autotune<A>(h));
     return H2_OK;
@@ -621,38 +631,65 @@ int upload(h2_handle h) {
 
 inline unsigned nblocks(int64_t n, int per) { return unsigned((n + per - 1) / per); }
 
-template <typename T, int D, int KIND, int NR>
+template <typename T, int D, int KIND, int NR, bool NEAR>
 void launch_leaf(h2_handle h, cudaStream_t s, int nrhs, int c0) {
     const h2::Host& H = h->host;
     const h2::Tree& t = H.tree;
     const h2::Packed& P = H.packed;
     const int64_t nleaf = t.nboxes(t.kappa);
     const T* vec = static_cast<const T*>(h->vec);
-    h2::k_leaf_fly<T, D, KIND, NR><<<unsigned(nleaf), 128, 0, s>>>(
+    h2::k_leaf_fly<T, D, KIND, NR, NEAR><<<unsigned(nleaf), 128, 0, s>>>(
         nleaf, P.nb, P.box_total, P.box_base[t.kappa], h->leaf_ptr, h->near_ptr, h->near_idx,
         h->rank, h->voff, h->uoff, h->ustride, static_cast<const T*>(h->ops), vec + P.u_base * nrhs,
         static_cast<const T*>(h->xs), t.N, vec + P.q_base * nrhs,
         static_cast<T*>(h->vec) + P.phi_base * nrhs, T(H.kern.param), T(H.kern.diag()), nrhs, c0);
 }
 
-template <typename T, int D, int KIND>
+template <typename T, int D, int KIND, bool NEAR>
 void launch_leaf_nr(h2_handle h, cudaStream_t s, int nrhs, int c0, int nr) {
     switch (nr) {
-        case 16: launch_leaf<T, D, KIND, 16>(h, s, nrhs, c0); break;
-        case 8: launch_leaf<T, D, KIND, 8>(h, s, nrhs, c0); break;
-        case 4: launch_leaf<T, D, KIND, 4>(h, s, nrhs, c0); break;
-        case 2: launch_leaf<T, D, KIND, 2>(h, s, nrhs, c0); break;
-        default: launch_leaf<T, D, KIND, 1>(h, s, nrhs, c0); break;
+        case 16: launch_leaf<T, D, KIND, 16, NEAR>(h, s, nrhs, c0); break;
+        case 8: launch_leaf<T, D, KIND, 8, NEAR>(h, s, nrhs, c0); break;
+        case 4: launch_leaf<T, D, KIND, 4, NEAR>(h, s, nrhs, c0); break;
+        case 2: launch_leaf<T, D, KIND, 2, NEAR>(h, s, nrhs, c0); break;
+        default: launch_leaf<T, D, KIND, 1, NEAR>(h, s, nrhs, c0); break;
     }
 }
 
-template <typename T, int D>
+// L2P plus the near field (NEAR), or L2P alone added to a near field already in phi
+template <typename T, int D, bool NEAR = true>
 void launch_leaf_d(h2_handle h, cudaStream_t s, int nrhs, int c0, int nr) {
     switch (h->host.kern.kind) {
-        case 0: launch_leaf_nr<T, D, 0>(h, s, nrhs, c0, nr); break;
-        case 1: launch_leaf_nr<T, D, 1>(h, s, nrhs, c0, nr); break;
-        case 2: launch_leaf_nr<T, D, 2>(h, s, nrhs, c0, nr); break;
-        default: launch_leaf_nr<T, D, 3>(h, s, nrhs, c0, nr); break;
+        case 0: launch_leaf_nr<T, D, 0, NEAR>(h, s, nrhs, c0, nr); break;
+        case 1: launch_leaf_nr<T, D, 1, NEAR>(h, s, nrhs, c0, nr); break;
+        case 2: launch_leaf_nr<T, D, 2, NEAR>(h, s, nrhs, c0, nr); break;
+        default: launch_leaf_nr<T, D, 3, NEAR>(h, s, nrhs, c0, nr); break;
+    }
+}
+
+// the near field alone, in double-float arithmetic (fp64 storage; 1/r, IMQ)
+template <int D, int KIND, int NR>
+void launch_near_df(h2_handle h, cudaStream_t s, int nrhs, int c0) {
+    const h2::Host& H = h->host;
+    const h2::Tree& t = H.tree;
+    const h2::Packed& P = H.packed;
+    const int64_t nleaf = t.nboxes(t.kappa);
+    double* vec = static_cast<double*>(h->vec);
+    const double c = H.kern.param;
+    h2::k_near_df<D, KIND, NR><<<unsigned(nleaf), 128, 0, s>>>(
+        nleaf, h->leaf_ptr, h->near_ptr, h->near_idx, static_cast<const double*>(h->xs), t.N,
+        vec + P.q_base * nrhs, vec + P.phi_base * nrhs, KIND == 2 ? 1.0 / (c * c) : 0.0, H.kern.diag(),
+        nrhs, c0);
+}
+
+template <int D, int KIND>
+void launch_near_df_nr(h2_handle h, cudaStream_t s, int nrhs, int c0, int nr) {
+    switch (nr) {
+        case 16: launch_near_df<D, KIND, 16>(h, s, nrhs, c0); break;
+        case 8: launch_near_df<D, KIND, 8>(h, s, nrhs, c0); break;
+        case 4: launch_near_df<D, KIND, 4>(h, s, nrhs, c0); break;
+        case 2: launch_near_df<D, KIND, 2>(h, s, nrhs, c0); break;
+        default: launch_near_df<D, KIND, 1>(h, s, nrhs, c0); break;
     }
 }
 
@@ -767,6 +804,25 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
         h2::k_gather<A><<<nblocks(t.N * nrhs, 256), 256, 0, s>>>(X, ldx, nrhs, h->perm, q, t.N);
     else
         h2::k_gather_t<A><<<nblocks(t.N, h2::kTransRows), 256, 0, s>>>(X, ldx, nrhs, h->iperm, q, t.N);
+    // fp64 near field on the fly in double-float arithmetic, on the side stream
+    // from here (q in tree order) to the L2P step
+    const bool near_side = std::is_same<A, h2::F64>::value && h->side && !P.near_stored;
+    if (near_side) {
+        H2_CUDA(cudaEventRecord(h->ev_fork, s));
+        H2_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        for (const auto& tl : tiles) {
+            ++nl;
+            const int kind = H.kern.kind;
+            if (d == 2) {
+                if (kind == 1) launch_near_df_nr<2, 1>(h, h->side, nrhs, tl.first, tl.second);
+                else launch_near_df_nr<2, 2>(h, h->side, nrhs, tl.first, tl.second);
+            } else {
+                if (kind == 1) launch_near_df_nr<3, 1>(h, h->side, nrhs, tl.first, tl.second);
+                else launch_near_df_nr<3, 2>(h, h->side, nrhs, tl.first, tl.second);
+            }
+        }
+        H2_CUDA(cudaEventRecord(h->ev_join, h->side));
+    }
     mark(h, s, ST_P2M);
     rows(h->p2m, 0);
     mark(h, s, ST_M2M);
@@ -793,10 +849,16 @@ int matvec_one(h2_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy
         rows(h->leaf, 0);
     } else if constexpr (!std::is_same<A, h2::DF>::value && !std::is_same<A, h2::BF16>::value) {
         using T = typename A::V;
+        if (near_side) H2_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
         for (const auto& tl : tiles) {
             ++nl;
-            if (d == 2) launch_leaf_d<T, 2>(h, s, nrhs, tl.first, tl.second);
-            else launch_leaf_d<T, 3>(h, s, nrhs, tl.first, tl.second);
+            if (near_side) {
+                if (d == 2) launch_leaf_d<T, 2, false>(h, s, nrhs, tl.first, tl.second);
+                else launch_leaf_d<T, 3, false>(h, s, nrhs, tl.first, tl.second);
+            } else {
+                if (d == 2) launch_leaf_d<T, 2>(h, s, nrhs, tl.first, tl.second);
+                else launch_leaf_d<T, 3>(h, s, nrhs, tl.first, tl.second);
+            }
         }
     }
     mark(h, s, ST_LOWRANK);
@@ -1250,6 +1312,9 @@ void h2_destroy(h2_handle h) {
         for (void* p : h->gm_allocs) cudaFree(p);
         for (auto& e : h->ev_pool) cudaEventDestroy(e);
         if (h->tc_err_host) cudaFreeHost(h->tc_err_host);
+        if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        if (h->ev_join) cudaEventDestroy(h->ev_join);
+        if (h->side) cudaStreamDestroy(h->side);
     }
     delete h;
 }

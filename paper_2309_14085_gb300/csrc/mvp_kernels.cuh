@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(256) k_rowgemv1(
 // tile; one CTA per leaf, one target per thread; the kernel value of each pair
 // is evaluated once and applied to all NR columns; source points staged
 // through shared memory.
-template <typename T, int D, int KIND, int NR>
+template <typename T, int D, int KIND, int NR, bool NEAR = true>
 __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t leaf_base,
                            const int64_t* __restrict__ leaf_ptr, const int64_t* __restrict__ near_ptr,
                            const int64_t* __restrict__ near_idx, const int32_t* __restrict__ rank,
@@ -510,7 +510,7 @@ __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t lea
                 }
             }
         }
-        for (int64_t e = near_ptr[L]; e < near_ptr[L + 1]; ++e) {
+        for (int64_t e = near_ptr[L]; NEAR && e < near_ptr[L + 1]; ++e) {
             const int64_t Y = near_idx[e];
             const int64_t s0 = leaf_ptr[Y];
             const int ms = int(leaf_ptr[Y + 1] - s0);
@@ -541,7 +541,140 @@ __global__ void k_leaf_fly(int64_t nleaf, int nb, int64_t box_total, int64_t lea
         }
         if (active) {
 #pragma unroll
-            for (int c = 0; c < NR; ++c) phi[(p0 + i) * nrhs + c0 + c] = acc[c];
+            for (int c = 0; c < NR; ++c) {
+                T* o = phi + (p0 + i) * nrhs + c0 + c;
+                *o = NEAR ? acc[c] : *o + acc[c];      // without NEAR: added to the near field
+            }
+        }
+    }
+}
+
+// ---- near field on the fly in double-float arithmetic (fp64 storage) -------------
+// phi_X = sum_{X' in N(X)} K_{t^X, s^X'} q_X' for 1/r and the inverse
+// multiquadric without the FP64 pipe: coordinates and charges are split into
+// float pairs (hi + lo, 48-bit significand) once per staged point, and every
+// pair's kernel value is formed in double-float arithmetic on the FP32 pipe --
+// the differences and squares with Knuth's two-sum and the FMA product
+// (Dekker), 1/sqrt(t) as one Newton step y0 + y0 (1 - t y0^2) / 2 from the
+// fp32 rsqrtf seed (whose relative error ~2^-22 the step squares) -- and
+// accumulated with the charges in double-float.  Per kernel value ~2^-44 of
+// relative error, where the fp64 path (sqrt and division on the FP64 pipe,
+// 1/64 of the FP32 rate on this GPU) rounds to 2^-53.  One CTA per leaf, one
+// target per thread, sources staged through shared memory; writes phi (=).
+namespace dd {
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return F2{s, b - (s - a)};
+}
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return F2{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ F2 split(double x) {
+    const float hi = __double2float_rn(x);
+    return F2{hi, __double2float_rn(x - double(hi))};
+}
+__device__ __forceinline__ F2 sub(F2 a, F2 b) {
+    F2 s = two_sum(a.hi, -b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo - b.lo));
+}
+__device__ __forceinline__ F2 add(F2 a, F2 b) {
+    F2 s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ F2 sqr(F2 a) {
+    const float p = a.hi * a.hi;
+    float e = fmaf(a.hi, a.hi, -p);
+    e = fmaf(2.0f * a.hi, a.lo, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ F2 mul(F2 a, F2 b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+// 1 / sqrt(t), t > 0: y1 = y0 + y0 h with h = (1 - t y0^2) / 2 and y0 = rsqrtf(t.hi)
+__device__ __forceinline__ F2 rsqrt(F2 t) {
+    const float y0 = rsqrtf(t.hi);
+    const float p = y0 * y0;
+    const F2 y2 = F2{p, fmaf(y0, y0, -p)};                      // y0^2 exactly
+    const F2 r = sub(F2{1.0f, 0.0f}, mul(t, y2));               // 1 - t y0^2, tiny
+    const float h = 0.5f * (r.hi + r.lo);
+    return fast_two_sum(y0, y0 * h);
+}
+}  // namespace dd
+
+template <int D, int KIND, int NR>
+__global__ void k_near_df(int64_t nleaf, const int64_t* __restrict__ leaf_ptr,
+                          const int64_t* __restrict__ near_ptr, const int64_t* __restrict__ near_idx,
+                          const double* __restrict__ xs, int64_t N, const double* __restrict__ q,
+                          double* __restrict__ phi, double param2, double diag, int nrhs, int c0) {
+    static_assert(KIND == 1 || KIND == 2, "1/r or the inverse multiquadric");
+    constexpr int TILE = 128;
+    __shared__ dd::F2 sx[D][TILE];
+    __shared__ dd::F2 sq[TILE * NR];
+    const int64_t L = blockIdx.x;
+    if (L >= nleaf) return;
+    const int64_t p0 = leaf_ptr[L];
+    const int m = int(leaf_ptr[L + 1] - p0);
+    const dd::F2 p2 = dd::split(param2);
+    const float dg = float(diag);
+    for (int i0 = 0; i0 < m; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool active = i < m;
+        dd::F2 acc[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] = dd::F2{0.0f, 0.0f};
+        dd::F2 xi[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xi[k] = dd::split(active ? xs[k * N + p0 + i] : 0.0);
+        for (int64_t e = near_ptr[L]; e < near_ptr[L + 1]; ++e) {
+            const int64_t Y = near_idx[e];
+            const int64_t s0 = leaf_ptr[Y];
+            const int ms = int(leaf_ptr[Y + 1] - s0);
+            for (int j0 = 0; j0 < ms; j0 += TILE) {
+                const int nt = min(TILE, ms - j0);
+                __syncthreads();
+                for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) sx[k][j] = dd::split(xs[k * N + s0 + j0 + j]);
+#pragma unroll
+                    for (int c = 0; c < NR; ++c) sq[j * NR + c] = dd::split(q[(s0 + j0 + j) * nrhs + c0 + c]);
+                }
+                __syncthreads();
+                if (active) {
+                    for (int j = 0; j < nt; ++j) {
+                        dd::F2 r2 = dd::sqr(dd::sub(xi[0], sx[0][j]));
+#pragma unroll
+                        for (int k = 1; k < D; ++k) r2 = dd::add(r2, dd::sqr(dd::sub(xi[k], sx[k][j])));
+                        dd::F2 g;
+                        if (r2.hi == 0.0f) {
+                            g = dd::F2{dg, 0.0f};               // coincident points: the diagonal value
+                        } else if constexpr (KIND == 1) {
+                            g = dd::rsqrt(r2);
+                        } else {
+                            g = dd::rsqrt(dd::add(dd::F2{1.0f, 0.0f}, dd::mul(r2, p2)));
+                        }
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) {
+                            const dd::F2 gq = dd::mul(g, sq[j * NR + c]);
+                            const dd::F2 s = dd::two_sum(acc[c].hi, gq.hi);
+                            acc[c] = dd::F2{s.hi, acc[c].lo + (s.lo + gq.lo)};
+                        }
+                    }
+                }
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c)
+                phi[(p0 + i) * nrhs + c0 + c] = double(acc[c].hi) + double(acc[c].lo);
         }
     }
 }

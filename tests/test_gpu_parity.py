@@ -274,3 +274,25 @@ def test_chebyshev_grid_matern_matches_oracle(variant):
     ref = O.matvec(q)
     assert _maxrel(y, ref) <= F64_TOL
     _dense_bar(y, ref, dense.product("matern12", P, q), 1e-8)
+
+
+@pytest.mark.parametrize("kind,nrhs", [("invr", 1), ("invr", 5), ("imq", 1), ("imq", 16)])
+def test_fp64_near_field_on_the_fly_in_double_float(kind, nrhs):
+    """fp64 storage with the near field evaluated on the fly for 1/r and the
+    IMQ: the kernel values are formed in double-float arithmetic on the FP32
+    pipe (1/sqrt by one Newton step from the fp32 seed, ~2^-44 per value) on a
+    second stream beside the far-field steps.  Checked against the oracle
+    under the fp64 bar, and against the same handle's points with the near
+    field stored (the host's fp64 kernel values) under the same bar."""
+    N = 7000
+    P = inputs.points(N, 3, 81)
+    Q = inputs.rhs(N, nrhs, 82).reshape(N, nrhs)
+    kw = dict(leaf_size=48, tol=1e-8, kparam=0.3) if kind == "imq" else dict(leaf_size=48, tol=1e-8)
+    A = H2Matrix(P, kind, near="fly", **kw)
+    B = H2Matrix(P, kind, near="stored", **kw)
+    assert A.info()["near_stored"] == 0 and B.info()["near_stored"] == 1
+    y = A.matvec(_dev(Q)).cpu().numpy().reshape(N, nrhs)
+    z = B.matvec(_dev(Q)).cpu().numpy().reshape(N, nrhs)
+    ref = h2.H2(P, kind, n_max=48, eps=1e-8, param=kw.get("kparam", 0.1)).matvec(Q).reshape(N, nrhs)
+    print(f"df near {kind} nrhs {nrhs}: vs oracle {_maxrel(y, ref):.2e}, vs stored {_maxrel(y, z):.2e}")
+    assert _maxrel(y, ref) <= F64_TOL and _maxrel(y, z) <= F64_TOL
