@@ -573,7 +573,7 @@ def bench_served(args):
             o.update(extra)
         return o
 
-    def run_plain():
+    def run_plain(arr=arr, gid=gid):
         for g, m in enumerate(f64s):          # warm-up: Krylov workspace of each geometry
             m.gmres(torch.tensor(fs[g], device="cuda"), shift=sigma, rtol=rtol, restart=restart,
                     maxit=maxit)
@@ -593,7 +593,7 @@ def bench_served(args):
             res.append(st["rel_residual"])
         return summary(lat, its, res, time.perf_counter() - start)
 
-    def run_server(mats, residual):
+    def run_server(mats, residual, arr=arr, gid=gid):
         S = H2Server(mats, restart=restart, max_active=args.max_active, residual=residual)
         for g in range(len(mats)):            # warm-up: one request per geometry
             S.wait(S.submit(g, fs[g], shift=sigma, rtol=rtol, maxit=maxit))
@@ -633,13 +633,25 @@ def bench_served(args):
                                           "fp64_after_fallback": ops.count(2)}}
         return summary(lat, its, res, span, extra)
 
+    forms = [f for f in args.served_forms.split(",") if f]
     clocks = Clocks(0)
     clocks.start()
     time.sleep(0.3)
-    plain = run_plain()
-    served64 = run_server(f64s, None)
+    res = {}
+    if "plain" in forms:
+        res["plain_fp64"] = run_plain()
+    if "fp64" in forms:
+        res["served_fp64"] = run_server(f64s, None)
     mixed = run_server(dfs, f64s)
-    served32 = run_server(f32s, f64s)
+    res["served_df64"] = mixed
+    if "f32" in forms:
+        res["served_f32"] = run_server(f32s, f64s)
+    if args.sub_rate > 0:
+        # below saturation: latency without the queueing of the overload stream
+        a2, g2 = inputs.poisson_arrivals(args.sub_requests, args.sub_rate, len(geo), seed=4998)
+        res["served_df64_below_saturation"] = dict(run_server(dfs, f64s, a2, g2),
+                                                    arrival_rate_per_s=args.sub_rate,
+                                                    requests=args.sub_requests)
     clk = clocks.stop()
     out = {"metric": "served RBF solves/s (p50/p99 latency)", "value": mixed["solves_per_s"],
            "unit": "solves/s", "n_gpus": 1, "steps": len(arr), "warmup": len(geo),
@@ -654,9 +666,11 @@ def bench_served(args):
                       "geometries": [{"d": gm["d"], "N": gm["N"]} for gm in geo],
                       "build_seconds": round(build_s, 1), "device_bytes": dev_bytes,
                       "l2": "operators larger than L2 (no flush)"},
-           "clocks": clk, "served_df64": mixed, "served_f32": served32, "served_fp64": served64,
-           "plain_fp64": plain}
-    print(json.dumps(out))
+           "clocks": clk}
+    out.update(res)
+    if args.standalone:
+        print(json.dumps(out))
+    return out
 
 
 def main():
@@ -695,6 +709,17 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="served workload: arrivals per s")
     ap.add_argument("--max-active", type=int, default=16, help="served workload: active requests")
     ap.add_argument("--restart", type=int, default=1000, help="served workload: GMRES restart")
+    ap.add_argument("--served-forms", default="plain,fp64,df64,f32",
+                    help="served workload: forms beside the double-float server (comma list)")
+    ap.add_argument("--sub-rate", type=float, default=0.0,
+                    help="served workload: also a stream below saturation at this rate (req/s)")
+    ap.add_argument("--sub-requests", type=int, default=12, help="requests of that stream")
+    ap.add_argument("--with-batched", type=int, default=512,
+                    help="default workload: also the batched workload with this many instances (0: skip)")
+    ap.add_argument("--with-served", type=int, default=1,
+                    help="default workload: also a bounded sample of the served workload (0: skip)")
+    ap.add_argument("--with-near-fly", type=int, default=1,
+                    help="default workload: also the fp64 product with the near field on the fly")
     args = ap.parse_args()
     args.standalone = False
     if args.oracle_child:
@@ -709,6 +734,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
 
     if args.workload == "c5_served":
+        args.standalone = True
         bench_served(args)
         return
 
@@ -807,6 +833,43 @@ def main():
                 mr[mode] = {"error": str(e)[:300]}
             a3._handles = {}
         out["multi_rhs_tensor_cores"] = mr
+    default = args.workload == "c2_3d_invr_n262144"
+    if default and args.with_near_fly and args.storage == "f64":
+        # the same fp64 product with the near field evaluated in double-float
+        # arithmetic instead of streamed (2.3 GB less on the device)
+        a6 = argparse.Namespace(**vars(args))
+        a6.near, a6.steps, a6._handles = "fly", max(3, min(args.steps, 20)), {}
+        o6, _ = bench_ours(a6, rank, world)
+        r6 = o6["roofline"]
+        out["near_on_the_fly"] = {"value": o6["value"], "ms_per_step": o6["ms_per_step"],
+                                  "stage_ms": r6["stage_ms"], "m2l_frac": r6.get("frac"),
+                                  "whole_mvp": r6.get("whole_mvp"),
+                                  "device_bytes": o6["config"]["device_bytes"],
+                                  "accuracy": o6.get("accuracy"), "clocks": o6["clocks"],
+                                  "gpu_launches": o6["gpu_launches"]}
+        for m in a6._handles.values():
+            m.close()
+    for m in getattr(args, "_handles", {}).values():
+        m.close()
+    args._handles = {}
+    if default and args.with_batched > 0 and world == 1:
+        import torch
+        torch.cuda.empty_cache()
+        a4 = argparse.Namespace(**vars(args))
+        a4.instances, a4.storage, a4.steps, a4.warmup, a4.standalone = args.with_batched, "f32", 10, 3, False
+        o4 = bench_batched(a4)
+        out["batched"] = {k: o4[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "roofline",
+                                             "gpu_launches", "clocks", "tensor_cores")}
+    if default and args.with_served and world == 1:
+        import torch
+        torch.cuda.empty_cache()
+        a5 = argparse.Namespace(**vars(args))
+        a5.geometries, a5.requests, a5.rate, a5.served_forms = 4, 32, 200.0, "plain"
+        a5.sub_rate, a5.sub_requests, a5.standalone = 1.0, 12, False
+        o5 = bench_served(a5)
+        out["served"] = {k: v for k, v in o5.items()
+                         if k not in ("metric", "n_gpus", "warmup", "higher_is_better", "scaling",
+                                      "vs_baseline", "data")}
     if rank == 0:
         out["cpu_baseline"] = cpu_baselines(args.workload, args.cpu_seconds)
         print(json.dumps(out))

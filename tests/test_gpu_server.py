@@ -141,3 +141,39 @@ def test_precision_guards_route_requests_to_the_fp64_operator():
     assert _true_residual(A, x.cpu().numpy(), f, 1.0) <= 1.01e-8
     x, st = L.gmres(b, shift=1.0, rtol=1e-8, restart=100, maxit=3000, residual=A)
     assert st["converged"] == 1 and st["fallback"] == 0, st
+
+
+def test_served_solutions_match_a_dense_solve():
+    """Served solutions of (sigma I + K) x = f against a dense LU solve of the
+    exact system (the oracle's matrix and solver) on small geometries, for the
+    fp64 server and the mixed-precision one (double-float operators, fp64
+    residuals).  The bar follows from the perturbation bound
+    |x - x*| / |x*| <= cond (|K - K~| / |A| + rtol), with |K - K~| / |A| taken
+    as 10 eps and the condition number computed from the dense matrix."""
+    from oracle import dense, gmres
+    sigma, eps, rtol = 1e-2, 1e-8, 1e-8
+    specs = [(2, 1800, 911), (3, 2400, 912)]
+    geoms, f64s, dfs = [], [], []
+    for d, N, seed in specs:
+        P = inputs.points(N, d, seed)
+        geoms.append(P)
+        A = H2Matrix(P, "imq", leaf_size=48, tol=eps, kparam=0.1)
+        f64s.append(A)
+        dfs.append(A.convert("df64"))
+    for mats, residual in ((f64s, None), (dfs, f64s)):
+        S = H2Server(mats, restart=200, max_active=4, residual=residual)
+        tickets = [S.submit(g, _rhs(geoms[g]), shift=sigma, rtol=rtol, maxit=5000)
+                   for g in range(len(specs))]
+        for g, t in enumerate(tickets):
+            x, st = S.wait(t)
+            assert st["converged"] == 1 and st["rel_residual"] <= rtol, st
+            P = geoms[g]
+            M = sigma * np.eye(len(P)) + dense.matrix("imq", P, param=0.1)
+            xd = gmres.dense_solve(M, _rhs(P))
+            cond = np.linalg.cond(M)
+            err = np.linalg.norm(x[:len(P)] - xd) / np.linalg.norm(xd)
+            bar = cond * (10 * eps + rtol)
+            print(f"served {'fp64' if residual is None else 'df64+fp64'} geometry {g}: "
+                  f"error vs dense LU {err:.2e}, bar {bar:.2e} (cond {cond:.1e})")
+            assert err <= bar
+        S.close()
