@@ -106,6 +106,14 @@ typedef struct {
                               each rounded once to the storage; the host never holds
                               them, so host_only handles of this mode have no M2L
                               values and batches refuse them)                        */
+    int    pivots;         /* where the B2T / T2B pivot search runs (ACA of §3.6 inside
+                              Algorithm 1 and §5.1.1): 0 (default) = host threads;
+                              1 = the current CUDA device, one CTA per ACA problem
+                              of a level, with the host's operations in the host's
+                              order (the same pivots for 1/r and the IMQ; log r and
+                              exp(-r) use the device's log / exp and may differ in
+                              the last bit); a problem needing more than 1024
+                              crosses is solved on the host.  Not with host_only. */
 } h2_build_opts;
 
 typedef struct h2_handle_s* h2_handle;
@@ -127,7 +135,7 @@ typedef struct h2_handle_s* h2_handle;
  *
  * The tree (§3.1), the interaction lists (§3.5 / §3.3), the pivots (B2T NCA
  * Algorithm 1, T2B NCA §5.1.1, ACA §3.6) and the operators (§3.6.4) are built
- * on the host with OpenMP; the operators are then packed per level and copied
+ * on the host with OpenMP (the pivot search on the device with opts->pivots); the operators are then packed per level and copied
  * to the current CUDA device (synchronously, on the legacy default stream),
  * where m2l_mode 2 forms the coupling blocks instead of copying them.
  * Errors: H2_E_INVALID_ARG, H2_E_UNSUPPORTED (an option this storage or
@@ -244,6 +252,9 @@ typedef struct {
                                       evaluated from pivot coordinates, 2 stored
                                       (device-formed)                                    */
     int64_t m2l_entries;           /* entries of all T_{X,Y} (sum of rows x columns)     */
+    int64_t pivot_problems_device; /* ACA problems of the pivot search solved on the device */
+    int64_t pivot_problems_host;   /* ... and on the host                                  */
+    double  pivot_seconds;         /* wall time of the pivot search (part of build_seconds) */
 } h2_stats;
 
 /* h2_info -- fill *st (host).  Errors: H2_E_INVALID_ARG. */

@@ -26,6 +26,7 @@ NEAR = {None: 0, "fly": 1, "stored": 2}
 #: M2L coupling blocks: stored (formed on the host), evaluated in each product
 #: from the pivot coordinates (fp32 only), or stored and formed on the device
 M2L = {None: 0, "stored": 0, "fly": 1, "device": 2}
+PIVOTS = {"host": 0, "device": 1}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
 EXPORTED = ("h2_build", "h2_convert", "h2_release_host", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
@@ -41,7 +42,7 @@ class BuildOpts(ctypes.Structure):
                 ("domain_side", ctypes.c_double), ("threads", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("kparam", ctypes.c_double),
                 ("near_mode", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("m2l_mode", ctypes.c_int)]
+                ("m2l_mode", ctypes.c_int), ("pivots", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -61,7 +62,8 @@ class Stats(ctypes.Structure):
                 ("bytes_device", ctypes.c_int64), ("alg_bytes_per_rhs", ctypes.c_int64),
                 ("build_seconds", ctypes.c_double), ("tc_blocks", ctypes.c_int * 3),
                 ("tc_occupancy", ctypes.c_int * 3), ("m2l_fly", ctypes.c_int),
-                ("m2l_entries", ctypes.c_int64)]
+                ("m2l_entries", ctypes.c_int64), ("pivot_problems_device", ctypes.c_int64),
+                ("pivot_problems_host", ctypes.c_int64), ("pivot_seconds", ctypes.c_double)]
 
 
 class GmresStats(ctypes.Structure):
@@ -176,7 +178,8 @@ class H2Matrix:
 
     def __init__(self, points, kernel, leaf_size=64, tol=1e-8, variant="h2star", storage="f64",
                  eps_far=None, eps_ver=None, kappa=None, domain=None, threads=0,
-                 host_only=False, kparam=None, near=None, tensor_cores=False, m2l=None):
+                 host_only=False, kparam=None, near=None, tensor_cores=False, m2l=None,
+                 pivots="host"):
         P = np.ascontiguousarray(points, dtype=np.float64)
         if P.ndim != 2:
             raise ValueError("points must be N x d")
@@ -199,6 +202,7 @@ class H2Matrix:
         o.near_mode = NEAR[near]
         o.tensor_cores = int(tensor_cores)
         o.m2l_mode = M2L[m2l]
+        o.pivots = PIVOTS[pivots]
         h = ctypes.c_void_p()
         _check(lib().h2_build(P.ctypes.data, self.N, self.d, KERNELS[kernel], leaf_size, tol,
                               VARIANTS[variant], ctypes.byref(o), ctypes.byref(h)))

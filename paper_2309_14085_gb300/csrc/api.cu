@@ -971,6 +971,9 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
                                                     o.m2l_mode, &unsupported))
             return fail(unsupported ? H2_E_UNSUPPORTED : H2_E_INVALID_ARG, why);
     }
+    if (o.pivots < 0 || o.pivots > 1) return fail(H2_E_INVALID_ARG, "pivots must be 0 or 1");
+    if (o.pivots == 1 && o.host_only)
+        return fail(H2_E_INVALID_ARG, "the device pivot search needs a device (host_only set)");
     if (o.kappa < 0 || o.kappa > 20) return fail(H2_E_INVALID_ARG, "kappa out of range");
     if (o.eps_far < 0 || o.eps_far >= 1 || o.eps_ver < 0 || o.eps_ver >= 1)
         return fail(H2_E_INVALID_ARG, "eps_far / eps_ver must be in [0, 1)");
@@ -1004,10 +1007,18 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     H.m2l_dev = o.m2l_mode == 2;
     H.eps_far = o.eps_far > 0 ? o.eps_far : tol;
     H.eps_ver = o.eps_ver > 0 ? o.eps_ver : tol;
+    H.pivots_dev = o.pivots;
+    if (o.pivots == 1) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+            cudaGetLastError();
+            return fail(H2_E_NO_DEVICE, "no CUDA device for the pivot search");
+        }
+    }
     try {
         std::string e = h2::build_host(H, points, N, d, leaf_size, o.kappa,
                                        o.use_domain ? o.domain_lo : nullptr, o.domain_side, o.threads);
-        if (!e.empty()) return fail(H2_E_INVALID_ARG, e);
+        if (!e.empty()) return fail(e.rfind("CUDA: ", 0) == 0 ? H2_E_CUDA : H2_E_INVALID_ARG, e);
     } catch (const std::bad_alloc&) {
         return fail(H2_E_OOM, "host allocation failed during construction");
     }
@@ -1222,6 +1233,9 @@ int h2_info(h2_handle h, h2_stats* st) {
         st->tc_occupancy[k] = h->tc_occupancy[k];
     }
     st->m2l_fly = H.m2l_fly ? 1 : H.m2l_dev ? 2 : 0;
+    st->pivot_problems_device = H.piv_problems_dev;
+    st->pivot_problems_host = H.piv_problems_host;
+    st->pivot_seconds = H.pivot_seconds;
     st->m2l_entries = 0;
     for (int64_t k = 0; k < P.m2l.size(); ++k) {
         int64_t cols = 0;

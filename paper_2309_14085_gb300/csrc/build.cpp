@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -215,6 +216,38 @@ void build_lists(const Tree& t, Lists& L) {
 constexpr int kAcaLookahead = 2;
 constexpr double kAcaNoise = 0x1p-46;
 
+// The sums of the stopping estimate (|u|^2, |v|^2, u_l . u, v_l . v) in one
+// fixed order: the terms in segments of kSumSeg, each segment over 256 lanes
+// (lane p summing the segment's terms p, p + 256, p + 512, ... in turn) and
+// then over the lanes pairwise (p + w into p for w = 128, 64, ..., 1), and the
+// segment totals in segment order.  Products are fused multiply-adds (std::fma
+// rounds once on every host).  The device pivot search sums in the same
+// order with the same operations (one CTA per segment), so both take the same
+// stopping decisions bit for bit.
+constexpr int kSumLanes = 256;
+constexpr int64_t kSumSeg = 4096;
+
+double lane_tree(double* s) {
+    for (int w = kSumLanes / 2; w >= 1; w >>= 1)
+        for (int p = 0; p < w; ++p) s[p] = s[p] + s[p + w];
+    return s[0];
+}
+
+// sum_j a[j] * b[j] in the order above
+double lane_dot(const double* a, const double* b, int64_t n) {
+    double S = 0.0;
+    for (int64_t g0 = 0; g0 < n; g0 += kSumSeg) {
+        double s[kSumLanes] = {};
+        const int64_t e = std::min(n, g0 + kSumSeg);
+        for (int64_t j0 = g0; j0 < e; j0 += kSumLanes) {
+            const int m = int(std::min<int64_t>(kSumLanes, e - j0));
+            for (int p = 0; p < m; ++p) s[p] = std::fma(a[j0 + p], b[j0 + p], s[p]);
+        }
+        S = S + lane_tree(s);
+    }
+    return S;
+}
+
 struct AcaResult {
     std::vector<int> rows, cols;
     std::vector<std::vector<double>> us, vs;   // kept only when requested
@@ -280,7 +313,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         for (size_t l = 0; l < us.size(); ++l) {
             const double a = us[l][ir];
             const double* vl = vs[l].data();
-            for (int64_t j = 0; j < nJ; ++j) out_r[j] = out_r[j] - a * vl[j];
+            for (int64_t j = 0; j < nJ; ++j) out_r[j] = std::fma(-a, vl[j], out_r[j]);
         }
     };
     fresh_row(i, r);
@@ -306,12 +339,11 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         for (size_t l = 0; l < us.size(); ++l) {
             const double bb = vs[l][jb];
             const double* ul = us[l].data();
-            for (int64_t a = 0; a < nI; ++a) u[a] = u[a] - bb * ul[a];
+            for (int64_t a = 0; a < nI; ++a) u[a] = std::fma(-bb, ul[a], u[a]);
         }
         col_used[jb] = 1;
-        double uu = 0.0, vv = 0.0;
-        for (int64_t a = 0; a < nI; ++a) uu += u[a] * u[a];
-        for (int64_t j = 0; j < nJ; ++j) vv += v[j] * v[j];
+        const double uu = lane_dot(u.data(), u.data(), nI);
+        const double vv = lane_dot(v.data(), v.data(), nJ);
         // next row: first argmax of |u| over unused rows (the same choice the
         // step after the stopping test makes)
         int64_t ib = -1;
@@ -322,76 +354,72 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         }
         const bool fuse = bi > 0.0;
         // one pass over the previous crosses: v_l . v for the norm update and,
-        // when the next row is known, its residual (same order of operations
-        // as computing them separately).  Four crosses share a sweep over j:
-        // each v_l . v is still summed in j order and each rn[j] still takes
-        // its subtractions in l order, so the results are those of one cross
-        // at a time, while four independent addition chains hide the latency
-        // of the sequential sums.
+        // when the next row is known, its residual.  Four crosses share a sweep
+        // over j: each rn[j] takes its subtractions in l order and each v_l . v
+        // its terms in the order of lane_dot, so the results are those of one
+        // cross at a time.
         pv.assign(us.size(), 0.0);
         if (fuse)
             entry_row(ib, rn.data());
         const size_t np = us.size();
         size_t l = 0;
+        double s0[kSumLanes], s1[kSumLanes], s2[kSumLanes], s3[kSumLanes];
         for (; l + 4 <= np; l += 4) {
             const double *v0 = vs[l].data(), *v1 = vs[l + 1].data(), *v2 = vs[l + 2].data(),
                          *v3 = vs[l + 3].data();
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            if (fuse) {
-                const double a0 = us[l][ib], a1 = us[l + 1][ib], a2 = us[l + 2][ib],
-                             a3 = us[l + 3][ib];
-                for (int64_t j = 0; j < nJ; ++j) {
-                    double x = rn[j];
-                    x = x - a0 * v0[j];
-                    x = x - a1 * v1[j];
-                    x = x - a2 * v2[j];
-                    x = x - a3 * v3[j];
-                    rn[j] = x;
-                    const double vj = v[j];
-                    s0 += v0[j] * vj;
-                    s1 += v1[j] * vj;
-                    s2 += v2[j] * vj;
-                    s3 += v3[j] * vj;
+            const double a0 = fuse ? us[l][ib] : 0.0, a1 = fuse ? us[l + 1][ib] : 0.0,
+                         a2 = fuse ? us[l + 2][ib] : 0.0, a3 = fuse ? us[l + 3][ib] : 0.0;
+            for (int64_t g0 = 0; g0 < nJ; g0 += kSumSeg) {
+                std::fill(s0, s0 + kSumLanes, 0.0);
+                std::fill(s1, s1 + kSumLanes, 0.0);
+                std::fill(s2, s2 + kSumLanes, 0.0);
+                std::fill(s3, s3 + kSumLanes, 0.0);
+                const int64_t e = std::min(nJ, g0 + kSumSeg);
+                for (int64_t j0 = g0; j0 < e; j0 += kSumLanes) {
+                    const int m = int(std::min<int64_t>(kSumLanes, e - j0));
+                    const double *w0 = v0 + j0, *w1 = v1 + j0, *w2 = v2 + j0, *w3 = v3 + j0;
+                    const double* vj = v.data() + j0;
+                    if (fuse) {
+                        double* x = rn.data() + j0;
+                        for (int p = 0; p < m; ++p) {
+                            double y = x[p];
+                            y = std::fma(-a0, w0[p], y);
+                            y = std::fma(-a1, w1[p], y);
+                            y = std::fma(-a2, w2[p], y);
+                            y = std::fma(-a3, w3[p], y);
+                            x[p] = y;
+                        }
+                    }
+                    for (int p = 0; p < m; ++p) {
+                        s0[p] = std::fma(w0[p], vj[p], s0[p]);
+                        s1[p] = std::fma(w1[p], vj[p], s1[p]);
+                        s2[p] = std::fma(w2[p], vj[p], s2[p]);
+                        s3[p] = std::fma(w3[p], vj[p], s3[p]);
+                    }
                 }
-            } else {
-                for (int64_t j = 0; j < nJ; ++j) {
-                    const double vj = v[j];
-                    s0 += v0[j] * vj;
-                    s1 += v1[j] * vj;
-                    s2 += v2[j] * vj;
-                    s3 += v3[j] * vj;
-                }
+                pv[l] = pv[l] + lane_tree(s0);
+                pv[l + 1] = pv[l + 1] + lane_tree(s1);
+                pv[l + 2] = pv[l + 2] + lane_tree(s2);
+                pv[l + 3] = pv[l + 3] + lane_tree(s3);
             }
-            pv[l] = s0;
-            pv[l + 1] = s1;
-            pv[l + 2] = s2;
-            pv[l + 3] = s3;
         }
         for (; l < np; ++l) {
             const double* vl = vs[l].data();
-            double s = 0.0;
             if (fuse) {
                 const double a = us[l][ib];
-                for (int64_t j = 0; j < nJ; ++j) {
-                    rn[j] = rn[j] - a * vl[j];
-                    s += vl[j] * v[j];
-                }
-            } else {
-                for (int64_t j = 0; j < nJ; ++j) s += vl[j] * v[j];
+                for (int64_t j = 0; j < nJ; ++j) rn[j] = std::fma(-a, vl[j], rn[j]);
             }
-            pv[l] = s;
+            pv[l] = lane_dot(vl, v.data(), nJ);
         }
         double cross = 0.0;
         for (size_t l = 0; l < us.size(); ++l) {
-            double pu = 0.0;
-            const double* ul = us[l].data();
-            for (int64_t a = 0; a < nI; ++a) pu += ul[a] * u[a];
-            cross += pu * pv[l];
+            const double pu = lane_dot(us[l].data(), u.data(), nI);
+            cross = std::fma(pu, pv[l], cross);
         }
         S2 = S2 + 2.0 * cross + uu * vv;
         if (fuse) {
             const double a = u[ib];
-            for (int64_t j = 0; j < nJ; ++j) rn[j] = rn[j] - a * v[j];
+            for (int64_t j = 0; j < nJ; ++j) rn[j] = std::fma(-a, v[j], rn[j]);
         }
         us.emplace_back(u);
         vs.emplace_back(std::move(v));
@@ -478,7 +506,71 @@ void level_time(const char* what, int l, std::chrono::steady_clock::time_point t
                  std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
 }
 
-void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps, int lmin = 2) {
+// The ACA problems of one level: sets(X, I, J) fills box X's row set and search
+// set; its pivots go to tau[X] (rows) and sig[X] (columns), as tree positions.
+// With a device the problems run there (the same pivots) and the host solves
+// only those the device hands back; otherwise each runs on the host.
+template <class Sets>
+std::string level_pivots(Host& H, PivotDevice* dev, int64_t n, double eps, Sets sets,
+                         std::vector<std::vector<int64_t>>& tau,
+                         std::vector<std::vector<int64_t>>& sig) {
+    const Tree& t = H.tree;
+    if (!dev) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t X = 0; X < n; ++X) {
+            std::vector<int64_t> I, J;
+            sets(X, I, J);
+            AcaResult R;
+            aca(t, H.kern, I, J, eps, false, R);
+            for (int a : R.rows) tau[X].push_back(I[a]);
+            for (int a : R.cols) sig[X].push_back(J[a]);
+        }
+        H.piv_problems_host += n;
+        return "";
+    }
+    std::vector<std::vector<int64_t>> Is(n), Js(n);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t X = 0; X < n; ++X) sets(X, Is[X], Js[X]);
+    AcaSets S;
+    S.Iptr.assign(n + 1, 0);
+    S.Jptr.assign(n + 1, 0);
+    for (int64_t X = 0; X < n; ++X) {
+        S.Iptr[X + 1] = S.Iptr[X] + int64_t(Is[X].size());
+        S.Jptr[X + 1] = S.Jptr[X] + int64_t(Js[X].size());
+    }
+    S.Iidx.resize(size_t(S.Iptr[n]));
+    S.Jidx.resize(size_t(S.Jptr[n]));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t X = 0; X < n; ++X) {
+        std::copy(Is[X].begin(), Is[X].end(), S.Iidx.begin() + S.Iptr[X]);
+        std::copy(Js[X].begin(), Js[X].end(), S.Jidx.begin() + S.Jptr[X]);
+    }
+    AcaPivots P;
+    const std::string err = pivot_device_level(dev, H.kern, eps, S, P);
+    if (!err.empty()) return err;
+    int64_t redo = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : redo)
+    for (int64_t X = 0; X < n; ++X) {
+        if (P.redo[X]) {
+            AcaResult R;
+            aca(t, H.kern, Is[X], Js[X], eps, false, R);
+            for (int a : R.rows) tau[X].push_back(Is[X][a]);
+            for (int a : R.cols) sig[X].push_back(Js[X][a]);
+            ++redo;
+        } else {
+            for (int64_t e = P.ptr[X]; e < P.ptr[X + 1]; ++e) {
+                tau[X].push_back(Is[X][P.rows[e]]);
+                sig[X].push_back(Js[X][P.cols[e]]);
+            }
+        }
+    }
+    H.piv_problems_host += redo;
+    H.piv_problems_dev += n - redo;
+    return "";
+}
+
+std::string b2t(Host& H, PivotDevice* dev, Basis& B, const std::vector<Csr>& il, double eps,
+                int lmin = 2) {
     const Tree& t = H.tree;
     const int K = t.kappa, d = t.d;
     B.lmin = lmin;
@@ -487,12 +579,9 @@ void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps, int lm
     B.sig.assign(K + 1, {});
     for (int l = 0; l <= K; ++l) { B.tau[l].resize(t.nboxes(l)); B.sig[l].resize(t.nboxes(l)); }
     for (int l = K; l >= lmin; --l) {
-        const int64_t n = t.nboxes(l);
         const auto tl = std::chrono::steady_clock::now();
-#pragma omp parallel for schedule(dynamic, 1)
-        for (int64_t X = 0; X < n; ++X) {
-            std::vector<int64_t> I, J;
-            const Csr& L = il[l];
+        const Csr& L = il[l];
+        auto sets = [&](int64_t X, std::vector<int64_t>& I, std::vector<int64_t>& J) {
             if (l == K) {
                 for (int64_t p = t.begin(l, X); p < t.end(l, X); ++p) I.push_back(p);
                 for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
@@ -512,18 +601,15 @@ void b2t(const Host& H, Basis& B, const std::vector<Csr>& il, double eps, int lm
                     }
                 }
             }
-            AcaResult R;
-            aca(t, H.kern, I, J, eps, false, R);
-            auto& tau = B.tau[l][X];
-            auto& sig = B.sig[l][X];
-            for (int a : R.rows) tau.push_back(I[a]);
-            for (int a : R.cols) sig.push_back(J[a]);
-        }
+        };
+        const std::string err = level_pivots(H, dev, t.nboxes(l), eps, sets, B.tau[l], B.sig[l]);
+        if (!err.empty()) return err;
         level_time("b2t", l, tl);
     }
+    return "";
 }
 
-void t2b(const Host& H, Basis& B, const std::vector<Csr>& il, double eps) {
+std::string t2b(Host& H, PivotDevice* dev, Basis& B, const std::vector<Csr>& il, double eps) {
     const Tree& t = H.tree;
     const int K = t.kappa, d = t.d;
     B.lmin = 1;
@@ -532,12 +618,9 @@ void t2b(const Host& H, Basis& B, const std::vector<Csr>& il, double eps) {
     B.sig.assign(K + 1, {});
     for (int l = 0; l <= K; ++l) { B.tau[l].resize(t.nboxes(l)); B.sig[l].resize(t.nboxes(l)); }
     for (int l = 1; l <= K; ++l) {
-        const int64_t n = t.nboxes(l);
         const auto tl = std::chrono::steady_clock::now();
-#pragma omp parallel for schedule(dynamic, 1)
-        for (int64_t X = 0; X < n; ++X) {
-            std::vector<int64_t> I, J;
-            const Csr& L = il[l];
+        const Csr& L = il[l];
+        auto sets = [&](int64_t X, std::vector<int64_t>& I, std::vector<int64_t>& J) {
             for (int64_t p = t.begin(l, X); p < t.end(l, X); ++p) I.push_back(p);
             for (int64_t e = L.ptr[X]; e < L.ptr[X + 1]; ++e) {
                 const int64_t Y = L.idx[e];
@@ -547,13 +630,12 @@ void t2b(const Host& H, Basis& B, const std::vector<Csr>& il, double eps) {
                 const auto& sp = B.sig[l - 1][X >> d];
                 J.insert(J.end(), sp.begin(), sp.end());
             }
-            AcaResult R;
-            aca(t, H.kern, I, J, eps, false, R);
-            for (int a : R.rows) B.tau[l][X].push_back(I[a]);
-            for (int a : R.cols) B.sig[l][X].push_back(J[a]);
-        }
+        };
+        const std::string err = level_pivots(H, dev, t.nboxes(l), eps, sets, B.tau[l], B.sig[l]);
+        if (!err.empty()) return err;
         level_time("t2b", l, tl);
     }
+    return "";
 }
 
 // ---------------------------------------------------------------------------
@@ -987,20 +1069,34 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
     tick("tree");
     build_lists(H.tree, H.lists);
     tick("lists");
+    const auto tpiv = std::chrono::steady_clock::now();
+    H.piv_problems_dev = H.piv_problems_host = 0;
+    // the pivot search on the device when asked; the handle is closed on every
+    // return below
+    std::unique_ptr<PivotDevice, void (*)(PivotDevice*)> dev(nullptr, pivot_device_close);
+    if (H.pivots_dev) {
+        std::string e;
+        dev.reset(pivot_device_open(H.tree, e));
+        if (!dev) return e;
+    }
+    std::string perr;
     H.bases.clear();
     if (H.variant == 0 || H.variant == 1) {
         H.bases.emplace_back();
-        b2t(H, H.bases.back(), H.lists.far, H.eps_far);
+        perr = b2t(H, dev.get(), H.bases.back(), H.lists.far, H.eps_far);
+        if (!perr.empty()) return perr;
         H.bases.back().il_kind = 0;
     }
     if (H.variant == 0) {
         H.bases.emplace_back();
-        t2b(H, H.bases.back(), H.lists.ver, H.eps_ver);
+        perr = t2b(H, dev.get(), H.bases.back(), H.lists.ver, H.eps_ver);
+        if (!perr.empty()) return perr;
         H.bases.back().il_kind = 1;
     }
     if (H.variant == 2) {
         H.bases.emplace_back();
-        b2t(H, H.bases.back(), H.lists.sqrtd, H.eps_far);
+        perr = b2t(H, dev.get(), H.bases.back(), H.lists.sqrtd, H.eps_far);
+        if (!perr.empty()) return perr;
         H.bases.back().il_kind = 2;
     }
     if (H.variant == 3 || H.variant == 5) {
@@ -1023,17 +1119,21 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
         }
         H.bases.emplace_back();
         if (H.variant == 3)   // H2*(t) (App. C): one basis, T2B NCA over the whole IL_*
-            t2b(H, H.bases.back(), H.lists.star, H.eps_far);
+            perr = t2b(H, dev.get(), H.bases.back(), H.lists.star, H.eps_far);
         else                  // §4.1: B2T NCA over the whole IL_*, levels kappa .. 1
-            b2t(H, H.bases.back(), H.lists.star, H.eps_far, 1);
+            perr = b2t(H, dev.get(), H.bases.back(), H.lists.star, H.eps_far, 1);
+        if (!perr.empty()) return perr;
         H.bases.back().il_kind = 3;
     }
     if (H.variant == 4) {
         // H2_sqrt(d)(t) (App. B): one basis, T2B NCA over the strong-admissibility lists
         H.bases.emplace_back();
-        t2b(H, H.bases.back(), H.lists.sqrtd, H.eps_far);
+        perr = t2b(H, dev.get(), H.bases.back(), H.lists.sqrtd, H.eps_far);
+        if (!perr.empty()) return perr;
         H.bases.back().il_kind = 2;
     }
+    dev.reset();
+    H.pivot_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - tpiv).count();
     tick("pivots");
     for (Basis& B : H.bases) {
         std::string e = operators(H, B);

@@ -148,6 +148,10 @@ struct Packed {
 
 struct Host {
     KernelSpec kern;
+    int pivots_dev = 0;              // 1: B2T / T2B pivot search on the device
+    int64_t piv_problems_dev = 0;    // ACA problems the device solved
+    int64_t piv_problems_host = 0;   // ACA problems solved on the host
+    double pivot_seconds = 0;        // wall time of the pivot phase
     int variant = 0;
     int storage = 0;
     int near_mode = 0;               // 0 default, 1 on the fly, 2 stored
@@ -184,6 +188,33 @@ inline const char* combination_error(int storage, int variant, int near_mode, in
     if ((storage == 2 || storage == 3) && variant == 1) return "(H2+H)* is built for fp64 and fp32 storage";
     return nullptr;
 }
+
+// The ACA problems of one level of a pivot sweep: problem X has row set
+// Iidx[Iptr[X] .. Iptr[X+1]) and search set Jidx[Jptr[X] .. Jptr[X+1]), both
+// as tree positions.
+struct AcaSets {
+    std::vector<int64_t> Iptr{0}, Jptr{0};
+    std::vector<int32_t> Iidx, Jidx;
+};
+
+// Their pivots: rows[ptr[X] .. ptr[X+1]) are positions into problem X's row
+// set, cols the matching positions into its search set; redo[X] = 1 marks a
+// problem the device did not finish (more crosses than its workspace holds),
+// which the host then solves.
+struct AcaPivots {
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> rows, cols;
+    std::vector<char> redo;
+};
+
+// Pivot search on the current CUDA device (pivots.cu): the host's ACA, one
+// CTA per problem, the same pivots.  open() copies the tree-order
+// coordinates; every call blocks until its results are on the host.
+struct PivotDevice;
+PivotDevice* pivot_device_open(const Tree& t, std::string& err);
+void pivot_device_close(PivotDevice* p);
+std::string pivot_device_level(PivotDevice* p, const KernelSpec& G, double eps, const AcaSets& S,
+                               AcaPivots& out);
 
 // Construction (build.cpp).  Return "" on success or an error message.
 std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf_size,

@@ -66,6 +66,30 @@ def test_invalid_arguments_return_error_codes():
     assert b"NULL" in pkg.lib().h2_last_error()
 
 
+def test_device_pivot_option_is_checked_before_any_device_use():
+    """pivots = 1 asks for the device pivot search: refused with host_only
+    (no device may be touched) and, without a CUDA device, NO_DEVICE before
+    any construction work."""
+    P = inputs.points(300, 2, 2)
+    with pytest.raises(H2Error) as e:
+        H2Matrix(P, "invr", leaf_size=16, tol=1e-6, pivots="device", host_only=True)
+    assert e.value.code == -1
+    o = pkg.BuildOpts()
+    o.pivots = 2
+    h = ctypes.c_void_p()
+    assert pkg.lib().h2_build(P.ctypes.data, 300, 2, 1, 16, 1e-6, 0, ctypes.byref(o),
+                              ctypes.byref(h)) == -1
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if not has_gpu:
+        with pytest.raises(H2Error) as e:
+            H2Matrix(P, "invr", leaf_size=16, tol=1e-6, pivots="device")
+        assert e.value.code == -6
+
+
 def test_unsupported_combinations_are_rejected():
     P = inputs.points(300, 2, 2)
     with pytest.raises(H2Error) as e:
