@@ -403,6 +403,10 @@ def bench_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "operators larger than L2 (no flush)",
                    "build_seconds": round(build_s, 2),
+                   "pivot_search": {"where": "device" if info["pivot_problems_device"] else "host",
+                                    "seconds": round(info["pivot_seconds"], 2),
+                                    "aca_problems": info["pivot_problems_device"] +
+                                    info["pivot_problems_host"]},
                    "device_bytes": info["bytes_device"],
                    "autotuned_rows_per_warp": {"m2l": info["rw_m2l"], "leaf": info["rw_leaf"]},
                    "tc_persistent_ctas": info["tc_blocks"], "tc_occupancy_api": info["tc_occupancy"],

@@ -107,13 +107,16 @@ typedef struct {
                               them, so host_only handles of this mode have no M2L
                               values and batches refuse them)                        */
     int    pivots;         /* where the B2T / T2B pivot search runs (ACA of §3.6 inside
-                              Algorithm 1 and §5.1.1): 0 (default) = host threads;
-                              1 = the current CUDA device, one CTA per ACA problem
-                              of a level, with the host's operations in the host's
-                              order (the same pivots for 1/r and the IMQ; log r and
-                              exp(-r) use the device's log / exp and may differ in
-                              the last bit); a problem needing more than 1024
-                              crosses is solved on the host.  Not with host_only. */
+                              Algorithm 1 and §5.1.1): 0 (default) = the current CUDA
+                              device for 1/r and the IMQ unless host_only is set,
+                              else host threads; 1 = the device; 2 = host threads.  The device runs every
+                              ACA problem of a level together (one CTA per 4096-entry
+                              segment of a search set) with the host's operations in
+                              the host's order: the same pivots for 1/r and the IMQ
+                              (log r and exp(-r) use the device's log / exp and may
+                              differ in the last bit); a problem needing more than
+                              1024 crosses is solved on the host.  1 with host_only
+                              is an error.                                          */
 } h2_build_opts;
 
 typedef struct h2_handle_s* h2_handle;

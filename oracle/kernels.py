@@ -13,9 +13,53 @@ silent about coincident points).
 
 r is formed as sqrt(dx^2 + dy^2 [+ dz^2]) with the squares summed in
 coordinate order.
+
+log r and exp(-r) come from the platform C library, one call per entry
+(``libm.c``, compiled on first use): their last bit depends on the
+implementation, and on point sets with exact ties (tensor grids) it decides
+the ACA pivots (reading: the paper fixes no implementation; the oracle uses the
+C library's, which a C or C++ construction on the same platform shares).
 """
 
+import ctypes
+import os
+import subprocess
+import threading
+
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBM = None
+_LIBM_LOCK = threading.Lock()
+
+
+def _libm():
+    """The compiled libm.c (built into oracle/_build/ when missing or stale)."""
+    global _LIBM
+    with _LIBM_LOCK:
+        if _LIBM is None:
+            src = os.path.join(_HERE, "libm.c")
+            out_dir = os.path.join(_HERE, "_build")
+            lib = os.path.join(out_dir, "liboracle_libm.so")
+            if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+                os.makedirs(out_dir, exist_ok=True)
+                tmp = lib + ".%d.tmp" % os.getpid()
+                subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fno-builtin",
+                                "-ffp-contract=off", src, "-o", tmp, "-lm"], check=True)
+                os.replace(tmp, lib)
+            L = ctypes.CDLL(lib)
+            for f in (L.oracle_log, L.oracle_exp_neg):
+                f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long]
+                f.restype = None
+            _LIBM = L
+    return _LIBM
+
+
+def _c_elementwise(fn, r):
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    fn(r.ctypes.data, out.ctypes.data, r.size)
+    return out
 
 KINDS = ("log2d", "invr", "imq", "matern12")
 
@@ -27,13 +71,13 @@ def diagonal_value(kind):
 def G(kind, r, param=0.1):
     """The radial function G(r) for r > 0."""
     if kind == "log2d":
-        return np.log(r)
+        return _c_elementwise(_libm().oracle_log, r)
     if kind == "invr":
         return 1.0 / r
     if kind == "imq":
         return 1.0 / np.sqrt(1.0 + (r / param) ** 2)
     if kind == "matern12":
-        return np.exp(-r)
+        return _c_elementwise(_libm().oracle_exp_neg, r)
     raise ValueError(f"unknown kernel {kind!r}")
 
 

@@ -26,7 +26,9 @@ NEAR = {None: 0, "fly": 1, "stored": 2}
 #: M2L coupling blocks: stored (formed on the host), evaluated in each product
 #: from the pivot coordinates (fp32 only), or stored and formed on the device
 M2L = {None: 0, "stored": 0, "fly": 1, "device": 2}
-PIVOTS = {"host": 0, "device": 1}
+#: where the pivot search runs: by default the device for 1/r and the IMQ unless
+#: host_only (the host for log r and exp(-r)), or forced
+PIVOTS = {None: 0, "device": 1, "host": 2}
 STAGES = ("gather", "p2m", "m2m", "m2l", "l2l", "leaf", "lowrank", "scatter")
 EXPORTED = ("h2_build", "h2_convert", "h2_release_host", "h2_matvec", "h2_gmres", "h2_info", "h2_get_pivots", "h2_tree_order",
             "h2_profile", "h2_stage_times", "h2_last_error", "h2_destroy", "h2_batch_create",
@@ -179,7 +181,7 @@ class H2Matrix:
     def __init__(self, points, kernel, leaf_size=64, tol=1e-8, variant="h2star", storage="f64",
                  eps_far=None, eps_ver=None, kappa=None, domain=None, threads=0,
                  host_only=False, kparam=None, near=None, tensor_cores=False, m2l=None,
-                 pivots="host"):
+                 pivots=None):
         P = np.ascontiguousarray(points, dtype=np.float64)
         if P.ndim != 2:
             raise ValueError("points must be N x d")

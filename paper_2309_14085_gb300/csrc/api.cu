@@ -971,7 +971,7 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
                                                     o.m2l_mode, &unsupported))
             return fail(unsupported ? H2_E_UNSUPPORTED : H2_E_INVALID_ARG, why);
     }
-    if (o.pivots < 0 || o.pivots > 1) return fail(H2_E_INVALID_ARG, "pivots must be 0 or 1");
+    if (o.pivots < 0 || o.pivots > 2) return fail(H2_E_INVALID_ARG, "pivots must be 0, 1 or 2");
     if (o.pivots == 1 && o.host_only)
         return fail(H2_E_INVALID_ARG, "the device pivot search needs a device (host_only set)");
     if (o.kappa < 0 || o.kappa > 20) return fail(H2_E_INVALID_ARG, "kappa out of range");
@@ -1007,8 +1007,11 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     H.m2l_dev = o.m2l_mode == 2;
     H.eps_far = o.eps_far > 0 ? o.eps_far : tol;
     H.eps_ver = o.eps_ver > 0 ? o.eps_ver : tol;
-    H.pivots_dev = o.pivots;
-    if (o.pivots == 1) {
+    // by default on the device where its pivots are the host's bit for bit
+    // (1/r and the IMQ: correctly rounded operations only)
+    H.pivots_dev = o.pivots == 1 || (o.pivots == 0 && !o.host_only &&
+                                     (kernel == H2_KERNEL_INVR || kernel == H2_KERNEL_IMQ));
+    if (H.pivots_dev) {
         int ndev = 0;
         if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
             cudaGetLastError();

@@ -220,8 +220,11 @@ constexpr double kAcaNoise = 0x1p-46;
 // fixed order: the terms in segments of kSumSeg, each segment over 256 lanes
 // (lane p summing the segment's terms p, p + 256, p + 512, ... in turn) and
 // then over the lanes pairwise (p + w into p for w = 128, 64, ..., 1), and the
-// segment totals in segment order.  Products are fused multiply-adds (std::fma
-// rounds once on every host).  The device pivot search sums in the same
+// segment totals in segment order, the products fused into the additions
+// (std::fma rounds once on every host).  The residual entries themselves take
+// a rounded product and a rounded subtraction per cross, in cross order, as
+// the oracle does: their exact values decide the argmax ties (symmetric point
+// sets have many).  The device pivot search sums in the same
 // order with the same operations (one CTA per segment), so both take the same
 // stopping decisions bit for bit.
 constexpr int kSumLanes = 256;
@@ -313,7 +316,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         for (size_t l = 0; l < us.size(); ++l) {
             const double a = us[l][ir];
             const double* vl = vs[l].data();
-            for (int64_t j = 0; j < nJ; ++j) out_r[j] = std::fma(-a, vl[j], out_r[j]);
+            for (int64_t j = 0; j < nJ; ++j) out_r[j] = out_r[j] - a * vl[j];
         }
     };
     fresh_row(i, r);
@@ -339,7 +342,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         for (size_t l = 0; l < us.size(); ++l) {
             const double bb = vs[l][jb];
             const double* ul = us[l].data();
-            for (int64_t a = 0; a < nI; ++a) u[a] = std::fma(-bb, ul[a], u[a]);
+            for (int64_t a = 0; a < nI; ++a) u[a] = u[a] - bb * ul[a];
         }
         col_used[jb] = 1;
         const double uu = lane_dot(u.data(), u.data(), nI);
@@ -383,10 +386,10 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
                         double* x = rn.data() + j0;
                         for (int p = 0; p < m; ++p) {
                             double y = x[p];
-                            y = std::fma(-a0, w0[p], y);
-                            y = std::fma(-a1, w1[p], y);
-                            y = std::fma(-a2, w2[p], y);
-                            y = std::fma(-a3, w3[p], y);
+                            y = y - a0 * w0[p];
+                            y = y - a1 * w1[p];
+                            y = y - a2 * w2[p];
+                            y = y - a3 * w3[p];
                             x[p] = y;
                         }
                     }
@@ -407,7 +410,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
             const double* vl = vs[l].data();
             if (fuse) {
                 const double a = us[l][ib];
-                for (int64_t j = 0; j < nJ; ++j) rn[j] = std::fma(-a, vl[j], rn[j]);
+                for (int64_t j = 0; j < nJ; ++j) rn[j] = rn[j] - a * vl[j];
             }
             pv[l] = lane_dot(vl, v.data(), nJ);
         }
@@ -419,7 +422,7 @@ void aca(const Tree& t, const KernelSpec& G, const std::vector<int64_t>& I,
         S2 = S2 + 2.0 * cross + uu * vv;
         if (fuse) {
             const double a = u[ib];
-            for (int64_t j = 0; j < nJ; ++j) rn[j] = std::fma(-a, v[j], rn[j]);
+            for (int64_t j = 0; j < nJ; ++j) rn[j] = rn[j] - a * v[j];
         }
         us.emplace_back(u);
         vs.emplace_back(std::move(v));

@@ -6,10 +6,11 @@
 // first-row start, the same first-index argmax rules, the same noise floor,
 // the same look-ahead stopping rule, and the same IEEE operations on every
 // value -- kernel entries (1/r and the IMQ through correctly rounded square
-// roots and divisions), residual rows and columns (fused multiply-adds in
-// cross order) and the four sums of the stopping estimate in the host's fixed
-// order (segments of 4096 terms over 256 lanes, a pairwise tree per segment,
-// segment totals in order).  Its pivots are therefore the host's, index for
+// roots and divisions), residual rows and columns (a rounded product and a
+// rounded subtraction per cross, in cross order) and the four sums of the
+// stopping estimate in the host's fixed order (fused multiply-adds over
+// segments of 4096 terms on 256 lanes, a pairwise tree per segment, segment
+// totals in order).  Its pivots are therefore the host's, index for
 // index, for 1/r and the IMQ; log r and exp(-r) go through the device's
 // log / exp, which may differ from the host library's in the last bit, so
 // their pivots can differ where a comparison is that close.
@@ -32,12 +33,14 @@
 // on.  The host loop only launches; it reads one counter every eight steps to
 // see whether every problem has finished.  A problem that needs more crosses
 // than its workspace holds stops with a status and is run again with more
-// room (beyond 1024 crosses the host solves it).
+// room; beyond 1024 crosses, or when the device has no memory for its batch,
+// the host solves it.
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kNT) k_stepA(Lv L) {
             const int j = g * kSeg + threadIdx.x + kNT * m;
             if (j >= nJ) break;
             double val = entry(L, w, nI, s.i, nJ, j);
-            for (int l = 0; l < k; ++l) val = __fma_rn(-col[l], w.V[int64_t(l) * nJ + j], val);
+            for (int l = 0; l < k; ++l) val = __dsub_rn(val, __dmul_rn(col[l], w.V[int64_t(l) * nJ + j]));
             r[j] = val;
         }
     }
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(kNT) k_stepC(Lv L) {
             const int a = g * kSeg + threadIdx.x + kNT * m;
             if (a >= nI) break;
             double val = entry(L, w, nI, a, nJ, s.jb);
-            for (int l = 0; l < k; ++l) val = __fma_rn(-col[l], w.U[int64_t(l) * nI + a], val);
+            for (int l = 0; l < k; ++l) val = __dsub_rn(val, __dmul_rn(col[l], w.U[int64_t(l) * nI + a]));
             u[a] = val;
             part = __fma_rn(val, val, part);
             const double q = w.ur[a] ? -1.0 : fabs(val);
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(kNT) k_stepE(Lv L) {
                     for (int q = 0; q < kLC; ++q)
                         if (q < nl) {
                             const double wv = w.V[int64_t(c0 + q) * nJ + j];
-                            if (fuse) xr[m] = __fma_rn(-col[c0 + q], wv, xr[m]);
+                            if (fuse) xr[m] = __dsub_rn(xr[m], __dmul_rn(col[c0 + q], wv));
                             part[q] = __fma_rn(wv, vj[m], part[q]);
                         }
                 }
@@ -466,7 +469,7 @@ __global__ void __launch_bounds__(kNT) k_stepE(Lv L) {
 #pragma unroll
             for (int m = 0; m < kPer; ++m) {
                 const int j = j0 + kNT * m;
-                if (j < nJ) rn[j] = __fma_rn(-uib, vj[m], xr[m]);
+                if (j < nJ) rn[j] = __dsub_rn(xr[m], __dmul_rn(uib, vj[m]));
             }
         }
     } else {
@@ -618,7 +621,7 @@ namespace {
 
 // Runs the problems `ids` (all with capacity kc_of[X]) to completion on the
 // device; fills rank / rows / cols of the finished ones and status 1 for those
-// that ran out of crosses.
+// that ran out of crosses (2: no device memory for the batch).
 std::string run_batch(PivotDevice* dev, const KernelSpec& G, double eps, const AcaSets& S,
                       const std::vector<int64_t>& ids, const std::vector<int32_t>& kc_of,
                       std::vector<int32_t>& rank, std::vector<int32_t>& status,
@@ -667,7 +670,13 @@ std::string run_batch(PivotDevice* dev, const KernelSpec& G, double eps, const A
     const size_t total = al(b_prob) + al(b_st) + al(b_i) + al(b_j) + 2 * al(b_out) + al(b_mj) +
                          al(b_mi) + 2 * al(b_s0) + al(4) + b_ws;
     char* buf = nullptr;
-    PIV_CUDA(cudaMalloc(&buf, total));
+    if (cudaMalloc(&buf, total) != cudaSuccess) {
+        // no room for this batch now (other work holds the memory): the host
+        // solves its problems
+        cudaGetLastError();
+        for (int64_t X : ids) status[X] = 2;
+        return "";
+    }
     std::string err;
     auto run = [&]() -> std::string {
         char* q = buf;
@@ -770,6 +779,10 @@ std::string pivot_device_level(PivotDevice* dev, const KernelSpec& G, double eps
     out.cols.clear();
     out.redo.assign(n, 0);
     if (n <= 0) return "";
+    // one search at a time per process: each sizes its workspace from the
+    // free device memory
+    static std::mutex one_at_a_time;
+    std::lock_guard<std::mutex> lock(one_at_a_time);
     const int d = dev->d;
     std::vector<int32_t> rank(n, 0), status(n, 0), kc_of(n, 0);
     std::vector<std::vector<int32_t>> prow(n), pcol(n);
@@ -821,7 +834,9 @@ std::string pivot_device_level(PivotDevice* dev, const KernelSpec& G, double eps
             const std::string err = run_batch(dev, G, eps, S, ids, kc_of, rank, status, prow, pcol);
             if (!err.empty()) return err;
             for (int64_t X : ids)
-                if (status[X]) {
+                if (status[X] == 2) {
+                    out.redo[X] = 1;
+                } else if (status[X]) {
                     // ran out of crosses: again with the largest capacity, unless
                     // it had that already (the host then solves it)
                     if (pass == 0 && kc_of[X] < std::min<int64_t>(kKMax, std::min(nI_of(X), nJ_of(X))))

@@ -24,7 +24,7 @@ namespace h2 {
 namespace {
 
 // the last byte is the format version: raise it whenever fields() changes
-constexpr char kMagic[8] = {'H', '2', 'S', 'T', 'A', 'R', '\0', '\2'};
+constexpr char kMagic[8] = {'H', '2', 'S', 'T', 'A', 'R', '\0', '\3'};
 
 // Checksum of the byte stream: the bytes as little-endian 64-bit words w_k,
 // h <- (h xor w_k) * P (the 64-bit FNV prime, odd, so every step is a
@@ -197,6 +197,9 @@ template <class IO, class H> void fields(IO& io, H& h) {
     io.pod(h.eps_far);
     io.pod(h.eps_ver);
     io.pod(h.build_seconds);
+    io.pod(h.pivot_seconds);
+    io.pod(h.piv_problems_dev);
+    io.pod(h.piv_problems_host);
     io.pod(h.near_pairs);
     io.pod(h.near_evals);
     io.pod(h.lowrank_entries);

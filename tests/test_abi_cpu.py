@@ -75,7 +75,7 @@ def test_device_pivot_option_is_checked_before_any_device_use():
         H2Matrix(P, "invr", leaf_size=16, tol=1e-6, pivots="device", host_only=True)
     assert e.value.code == -1
     o = pkg.BuildOpts()
-    o.pivots = 2
+    o.pivots = 3
     h = ctypes.c_void_p()
     assert pkg.lib().h2_build(P.ctypes.data, 300, 2, 1, 16, 1e-6, 0, ctypes.byref(o),
                               ctypes.byref(h)) == -1
@@ -88,6 +88,11 @@ def test_device_pivot_option_is_checked_before_any_device_use():
         with pytest.raises(H2Error) as e:
             H2Matrix(P, "invr", leaf_size=16, tol=1e-6, pivots="device")
         assert e.value.code == -6
+    # host_only takes the host search by default; forcing it is accepted too
+    A = H2Matrix(P, "invr", leaf_size=16, tol=1e-6, host_only=True)
+    B = H2Matrix(P, "invr", leaf_size=16, tol=1e-6, host_only=True, pivots="host")
+    assert A.info()["pivot_problems_device"] == 0 and A.info()["pivot_problems_host"] > 0
+    assert np.array_equal(A.pivots(0, 2, 5)[0], B.pivots(0, 2, 5)[0])
 
 
 def test_unsupported_combinations_are_rejected():

@@ -1,4 +1,4 @@
-"""Pivot search on the device (h2_build_opts.pivots = 1).
+"""Pivot search on the device (h2_build_opts.pivots: the default of a device build).
 
 The B2T / T2B pivots are integer decisions (argmax positions and the ACA
 stopping rule of §3.6).  The device search takes the host's operations in the
@@ -8,8 +8,9 @@ the stopping sums in the host's fixed lane order -- so for 1/r and the IMQ its
 pivots must equal the host's index for index, in every variant, and the
 products built from them must then be equal bit for bit.  log r and exp(-r)
 use the device's log / exp (within an ulp of the host library), so there the
-pivots may differ where a comparison is that close; the representation must
-still meet the 10 eps bar against the exact product.  The host pivots are
+pivots may differ where a comparison is that close (on a Chebyshev grid's
+exact ties they do) and the default stays on the host; forced onto the device,
+the representation must be as accurate as the host-pivot one.  The host pivots are
 themselves pinned to the oracle's index for index (test_abi_cpu.py).
 """
 
@@ -59,7 +60,7 @@ EXACT = [
 @pytest.mark.parametrize("kind,d,N,n_max,eps,variant", EXACT)
 def test_device_pivots_equal_host_pivots(kind, d, N, n_max, eps, variant):
     P = inputs.points(N, d, 7100 + N)
-    H = H2Matrix(P, kind, leaf_size=n_max, tol=eps, variant=variant)
+    H = H2Matrix(P, kind, leaf_size=n_max, tol=eps, variant=variant, pivots="host")
     D = H2Matrix(P, kind, leaf_size=n_max, tol=eps, variant=variant, pivots="device")
     hi, di = H.info(), D.info()
     assert di["pivot_problems_device"] > 0 and hi["pivot_problems_device"] == 0
@@ -75,6 +76,23 @@ def test_device_pivots_equal_host_pivots(kind, d, N, n_max, eps, variant):
           "pivot seconds host %.2f device %.2f" % (hi["pivot_seconds"], di["pivot_seconds"]))
 
 
+@pytest.mark.parametrize("kind", ["invr", "imq"])
+def test_device_pivots_equal_host_pivots_on_a_chebyshev_grid(kind):
+    """18^3 Chebyshev points: a symmetric point set where many residual
+    entries tie exactly, so every first-index tie rule is exercised; with
+    correctly rounded kernel values the device breaks each tie as the host
+    does.  The default of a device build is the device search."""
+    P = inputs.chebyshev_grid(18, 3)
+    H = H2Matrix(P, kind, leaf_size=32, tol=1e-8, pivots="host")
+    D = H2Matrix(P, kind, leaf_size=32, tol=1e-8)
+    assert D.info()["pivot_problems_device"] > 0
+    ph, pd = _all_pivots(H), _all_pivots(D)
+    assert ph.keys() == pd.keys()
+    for key in ph:
+        assert np.array_equal(ph[key][0], pd[key][0]), key
+        assert np.array_equal(ph[key][1], pd[key][1]), key
+
+
 @pytest.mark.parametrize("kind,d,N,eps", [("log2d", 2, 20000, 1e-8), ("matern12", 3, 9000, 1e-6)])
 def test_device_pivots_with_library_log_exp(kind, d, N, eps):
     """log r / exp(-r): pivots agree with the host's up to last-bit kernel
@@ -83,6 +101,7 @@ def test_device_pivots_with_library_log_exp(kind, d, N, eps):
     P = inputs.points(N, d, 7300 + N)
     H = H2Matrix(P, kind, leaf_size=64, tol=eps)
     D = H2Matrix(P, kind, leaf_size=64, tol=eps, pivots="device")
+    assert H.info()["pivot_problems_device"] == 0     # the default for log r / exp(-r)
     ph, pd = _all_pivots(H), _all_pivots(D)
     same = sum(np.array_equal(ph[k][0], pd.get(k, ([], []))[0]) for k in ph)
     q = inputs.rhs(N, 1, 7400 + N).reshape(N)
