@@ -689,10 +689,10 @@ def main():
                     help="default workload only: also time the 64-RHS workload on the tensor "
                          "cores in these modes (comma list of f32 (3-term tf32 products of fp32 "
                          "operators), bf16; '' for none)")
-    ap.add_argument("--m2l", default="stored", choices=["stored", "fly", "device"],
-                    help="M2L blocks: stored (formed on the host), fly (fp32: evaluated "
-                         "from the pivot coordinates in each product), device (stored, "
-                         "formed on the device from the pivots)")
+    ap.add_argument("--m2l", default="device", choices=["stored", "fly", "device"],
+                    help="M2L blocks: device (default: stored, formed on the device from the "
+                         "pivots), stored (formed on the host and uploaded), fly (fp32: "
+                         "evaluated from the pivot coordinates in each product)")
     ap.add_argument("--near", default=None, choices=["fly", "stored"],
                     help="near field: evaluated in each product (fp64: double-float arithmetic "
                          "for 1/r and the IMQ) or stored blocks; default: the storage's default")
