@@ -115,8 +115,9 @@ typedef struct {
                               the host's order: the same pivots for 1/r and the IMQ
                               (log r and exp(-r) use the device's log / exp and may
                               differ in the last bit); a problem needing more than
-                              1024 crosses is solved on the host.  1 with host_only
-                              is an error.                                          */
+                              1024 crosses is solved on the host.  The (H2+H)* ACA
+                              blocks (Algorithm 3) go the same way.  1 with
+                              host_only is an error.                                */
 } h2_build_opts;
 
 typedef struct h2_handle_s* h2_handle;
@@ -255,7 +256,8 @@ typedef struct {
                                       evaluated from pivot coordinates, 2 stored
                                       (device-formed)                                    */
     int64_t m2l_entries;           /* entries of all T_{X,Y} (sum of rows x columns)     */
-    int64_t pivot_problems_device; /* ACA problems of the pivot search solved on the device */
+    int64_t pivot_problems_device; /* ACA problems solved on the device: the B2T / T2B pivot
+                                      search and the (H2+H)* blocks of Algorithm 3       */
     int64_t pivot_problems_host;   /* ... and on the host                                  */
     double  pivot_seconds;         /* wall time of the pivot search (part of build_seconds) */
 } h2_stats;

@@ -711,7 +711,10 @@ std::string operators(const Host& H, Basis& B) {
     return err;
 }
 
-void pure_aca(Host& H) {
+// (H2+H)*: one ACA per vertex-sharing pair with its crosses kept (Algorithm 3);
+// all pairs are independent, so with a device they run there as one set of
+// problems (the same crosses, bit for bit, as the host's for 1/r and the IMQ)
+std::string pure_aca(Host& H, PivotDevice* dev) {
     const Tree& t = H.tree;
     const int K = t.kappa;
     std::vector<std::pair<int, std::pair<int64_t, int64_t>>> pairs;
@@ -719,20 +722,20 @@ void pure_aca(Host& H) {
         for (int64_t X = 0; X < t.nboxes(l); ++X)
             for (int64_t e = H.lists.ver[l].ptr[X]; e < H.lists.ver[l].ptr[X + 1]; ++e)
                 pairs.push_back({l, {X, H.lists.ver[l].idx[e]}});
-    H.lowrank.assign(pairs.size(), LowRankBlock());
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t p = 0; p < int64_t(pairs.size()); ++p) {
+    const int64_t np = int64_t(pairs.size());
+    H.lowrank.assign(np, LowRankBlock());
+    auto sets = [&](int64_t p, std::vector<int64_t>& I, std::vector<int64_t>& J) {
         const int l = pairs[p].first;
         const int64_t X = pairs[p].second.first, Y = pairs[p].second.second;
-        std::vector<int64_t> I, J;
         for (int64_t a = t.begin(l, X); a < t.end(l, X); ++a) I.push_back(a);
         for (int64_t a = t.begin(l, Y); a < t.end(l, Y); ++a) J.push_back(a);
+    };
+    auto on_host = [&](int64_t p) {
+        std::vector<int64_t> I, J;
+        sets(p, I, J);
         AcaResult R;
         aca(t, H.kern, I, J, H.eps_ver, true, R);
         LowRankBlock& B = H.lowrank[p];
-        B.level = l;
-        B.X = X;
-        B.Y = Y;
         B.k = int(R.rows.size());
         B.U.resize(I.size() * size_t(B.k));
         B.V.resize(J.size() * size_t(B.k));
@@ -740,7 +743,58 @@ void pure_aca(Host& H) {
             std::copy(R.us[k].begin(), R.us[k].end(), B.U.begin() + size_t(k) * I.size());
             std::copy(R.vs[k].begin(), R.vs[k].end(), B.V.begin() + size_t(k) * J.size());
         }
+    };
+    for (int64_t p = 0; p < np; ++p) {
+        LowRankBlock& B = H.lowrank[p];
+        B.level = pairs[p].first;
+        B.X = pairs[p].second.first;
+        B.Y = pairs[p].second.second;
     }
+    if (!dev) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t p = 0; p < np; ++p) on_host(p);
+        H.piv_problems_host += np;
+        return "";
+    }
+    AcaSets S;
+    S.Iptr.assign(np + 1, 0);
+    S.Jptr.assign(np + 1, 0);
+    for (int64_t p = 0; p < np; ++p) {
+        const int l = pairs[p].first;
+        const int64_t X = pairs[p].second.first, Y = pairs[p].second.second;
+        S.Iptr[p + 1] = S.Iptr[p] + (t.end(l, X) - t.begin(l, X));
+        S.Jptr[p + 1] = S.Jptr[p] + (t.end(l, Y) - t.begin(l, Y));
+    }
+    S.Iidx.resize(size_t(S.Iptr[np]));
+    S.Jidx.resize(size_t(S.Jptr[np]));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < np; ++p) {
+        const int l = pairs[p].first;
+        const int64_t X = pairs[p].second.first, Y = pairs[p].second.second;
+        for (int64_t a = t.begin(l, X); a < t.end(l, X); ++a) S.Iidx[S.Iptr[p] + a - t.begin(l, X)] = int32_t(a);
+        for (int64_t a = t.begin(l, Y); a < t.end(l, Y); ++a) S.Jidx[S.Jptr[p] + a - t.begin(l, Y)] = int32_t(a);
+    }
+    AcaPivots P;
+    const std::string err = pivot_device_level(dev, H.kern, H.eps_ver, S, P, true);
+    if (!err.empty()) return err;
+    int64_t redo = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : redo)
+    for (int64_t p = 0; p < np; ++p) {
+        if (P.redo[p]) {
+            on_host(p);
+            ++redo;
+            continue;
+        }
+        LowRankBlock& B = H.lowrank[p];
+        const int64_t nI = S.Iptr[p + 1] - S.Iptr[p], nJ = S.Jptr[p + 1] - S.Jptr[p];
+        B.k = int(P.ptr[p + 1] - P.ptr[p]);
+        const std::vector<double>& f = P.factors[p];
+        B.U.assign(f.begin(), f.begin() + size_t(B.k) * size_t(nI));
+        B.V.assign(f.begin() + size_t(B.k) * size_t(nI), f.begin() + size_t(B.k) * size_t(nI + nJ));
+    }
+    H.piv_problems_host += redo;
+    H.piv_problems_dev += np - redo;
+    return "";
 }
 
 // ---------------------------------------------------------------------------
@@ -1135,14 +1189,17 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
         if (!perr.empty()) return perr;
         H.bases.back().il_kind = 2;
     }
-    dev.reset();
     H.pivot_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - tpiv).count();
     tick("pivots");
     for (Basis& B : H.bases) {
         std::string e = operators(H, B);
         if (!e.empty()) return e;
     }
-    if (H.variant == 1) pure_aca(H);
+    if (H.variant == 1) {
+        perr = pure_aca(H, dev.get());
+        if (!perr.empty()) return perr;
+    }
+    dev.reset();
     tick("operators");
     pack(H);
     // the packed array now holds every operator: keep only pivots and sizes

@@ -200,11 +200,13 @@ struct AcaSets {
 // Their pivots: rows[ptr[X] .. ptr[X+1]) are positions into problem X's row
 // set, cols the matching positions into its search set; redo[X] = 1 marks a
 // problem the device did not finish (more crosses than its workspace holds),
-// which the host then solves.
+// which the host then solves.  With keep, factors[X] holds the kept crosses:
+// U (rank x |I|) then V (rank x |J|), cross-major.
 struct AcaPivots {
     std::vector<int64_t> ptr;
     std::vector<int32_t> rows, cols;
     std::vector<char> redo;
+    std::vector<std::vector<double>> factors;
 };
 
 // Pivot search on the current CUDA device (pivots.cu): the host's ACA, one
@@ -214,7 +216,7 @@ struct PivotDevice;
 PivotDevice* pivot_device_open(const Tree& t, std::string& err);
 void pivot_device_close(PivotDevice* p);
 std::string pivot_device_level(PivotDevice* p, const KernelSpec& G, double eps, const AcaSets& S,
-                               AcaPivots& out);
+                               AcaPivots& out, bool keep = false);
 
 // Construction (build.cpp).  Return "" on success or an error message.
 std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf_size,

@@ -577,6 +577,24 @@ __global__ void __launch_bounds__(kNT) k_stepF(Lv L) {
     }
 }
 
+// the kept crosses of finished problems, packed: problem b's U (rank x |I|)
+// then V (rank x |J|), cross-major (the (H2+H)* factors, point index fastest)
+__global__ void __launch_bounds__(kNT) k_pack_factors(const double* __restrict__ ws,
+                                                      const Prob* __restrict__ prob,
+                                                      const int32_t* __restrict__ rk,
+                                                      const int64_t* __restrict__ foff,
+                                                      double* __restrict__ out, int d) {
+    const Prob P = prob[blockIdx.x];
+    const int r = rk[blockIdx.x];
+    if (r <= 0) return;
+    const double* U = ws + P.ws + int64_t(d) * (P.nI + P.nJ);
+    const double* V = U + int64_t(P.kc) * P.nI;
+    double* o = out + foff[blockIdx.x];
+    const int64_t nu = int64_t(r) * P.nI, nv = int64_t(r) * P.nJ;
+    for (int64_t i = threadIdx.x; i < nu; i += kNT) o[i] = U[i];
+    for (int64_t i = threadIdx.x; i < nv; i += kNT) o[nu + i] = V[i];
+}
+
 #define PIV_CUDA(call)                                                              \
     do {                                                                            \
         const cudaError_t e_ = (call);                                              \
@@ -625,7 +643,8 @@ namespace {
 std::string run_batch(PivotDevice* dev, const KernelSpec& G, double eps, const AcaSets& S,
                       const std::vector<int64_t>& ids, const std::vector<int32_t>& kc_of,
                       std::vector<int32_t>& rank, std::vector<int32_t>& status,
-                      std::vector<std::vector<int32_t>>& prow, std::vector<std::vector<int32_t>>& pcol) {
+                      std::vector<std::vector<int32_t>>& prow, std::vector<std::vector<int32_t>>& pcol,
+                      bool keep, std::vector<std::vector<double>>& fac) {
     const int d = dev->d;
     const int64_t np = int64_t(ids.size());
     std::vector<Prob> probs(np);
@@ -762,6 +781,37 @@ std::string run_batch(PivotDevice* dev, const KernelSpec& G, double eps, const A
                 if (a < 0 || a >= probs[b].nJ) return "device pivot search returned a bad column";
             rank[X] = rk;
         }
+        if (keep) {
+            std::vector<int64_t> foff(np + 1, 0);
+            std::vector<int32_t> rks(np, 0);
+            for (int64_t b = 0; b < np; ++b) {
+                rks[b] = status[ids[b]] ? 0 : rank[ids[b]];
+                foff[b + 1] = foff[b] + int64_t(rks[b]) * (probs[b].nI + probs[b].nJ);
+            }
+            if (foff[np] > 0) {
+                char* fb = nullptr;
+                const size_t b_f = 8 * size_t(foff[np]);
+                PIV_CUDA(cudaMalloc(&fb, al(b_f) + al(8 * size_t(np + 1)) + al(4 * size_t(np))));
+                double* d_f = reinterpret_cast<double*>(fb);
+                int64_t* d_fo = reinterpret_cast<int64_t*>(fb + al(b_f));
+                int32_t* d_rk = reinterpret_cast<int32_t*>(fb + al(b_f) + al(8 * size_t(np + 1)));
+                std::vector<double> hf(foff[np]);
+                auto pack = [&]() -> std::string {
+                    PIV_CUDA(cudaMemcpyAsync(d_fo, foff.data(), 8 * size_t(np + 1), cudaMemcpyHostToDevice, sm));
+                    PIV_CUDA(cudaMemcpyAsync(d_rk, rks.data(), 4 * size_t(np), cudaMemcpyHostToDevice, sm));
+                    k_pack_factors<<<unsigned(np), kNT, 0, sm>>>(d_ws, d_prob, d_rk, d_fo, d_f, d);
+                    PIV_CUDA(cudaGetLastError());
+                    PIV_CUDA(cudaMemcpyAsync(hf.data(), d_f, b_f, cudaMemcpyDeviceToHost, sm));
+                    PIV_CUDA(cudaStreamSynchronize(sm));
+                    return "";
+                };
+                const std::string e = pack();
+                cudaFree(fb);
+                if (!e.empty()) return e;
+                for (int64_t b = 0; b < np; ++b)
+                    if (rks[b] > 0) fac[ids[b]].assign(hf.begin() + foff[b], hf.begin() + foff[b + 1]);
+            }
+        }
         return "";
     };
     err = run();
@@ -772,12 +822,13 @@ std::string run_batch(PivotDevice* dev, const KernelSpec& G, double eps, const A
 }  // namespace
 
 std::string pivot_device_level(PivotDevice* dev, const KernelSpec& G, double eps, const AcaSets& S,
-                               AcaPivots& out) {
+                               AcaPivots& out, bool keep) {
     const int64_t n = int64_t(S.Iptr.size()) - 1;
     out.ptr.assign(n + 1, 0);
     out.rows.clear();
     out.cols.clear();
     out.redo.assign(n, 0);
+    out.factors.assign(keep ? n : 0, {});
     if (n <= 0) return "";
     // one search at a time per process: each sizes its workspace from the
     // free device memory
@@ -831,7 +882,8 @@ std::string pivot_device_level(PivotDevice* dev, const KernelSpec& G, double eps
                 ++at;
             }
             if (ids.empty()) continue;
-            const std::string err = run_batch(dev, G, eps, S, ids, kc_of, rank, status, prow, pcol);
+            const std::string err = run_batch(dev, G, eps, S, ids, kc_of, rank, status, prow, pcol,
+                                              keep, out.factors);
             if (!err.empty()) return err;
             for (int64_t X : ids)
                 if (status[X] == 2) {

@@ -112,3 +112,27 @@ def test_device_pivots_with_library_log_exp(kind, d, N, eps):
     print(kind, "boxes with equal pivots", same, "of", len(ph), "RE host %.3e device %.3e" % (re_h, re_d))
     assert same >= 0.9 * len(ph)
     assert re_d <= 1.25 * re_h and re_d <= 30 * eps
+
+
+@pytest.mark.parametrize("kind,d,N,variant", [("invr", 3, 5000, "h2star"), ("invr", 3, 5000, "h2plush"),
+                                              ("imq", 2, 6000, "h2plush")])
+def test_device_construction_equals_the_hosts_byte_for_byte(tmp_path, kind, d, N, variant):
+    """The whole construction written by h2_save -- every pivot, every operator
+    and, for (H2+H)*, every kept ACA factor of Algorithm 3 (those pairs run on
+    the device too) -- is the same with the device search as with the host's.
+    Bytes 60-91 hold the build and pivot-search times and the device / host
+    problem counts, the last 8 the checksum."""
+    P = inputs.points(N, d, 7700 + N)
+    H = H2Matrix(P, kind, leaf_size=32, tol=1e-6, variant=variant, pivots="host")
+    D = H2Matrix(P, kind, leaf_size=32, tol=1e-6, variant=variant)
+    hi, di = H.info(), D.info()
+    assert hi["pivot_problems_device"] == 0
+    assert di["pivot_problems_host"] == 0
+    assert di["pivot_problems_device"] == hi["pivot_problems_host"]
+    if variant == "h2plush":
+        assert di["lowrank_pairs"] > 0 and di["bytes_lowrank"] == hi["bytes_lowrank"]
+    fa, fb = str(tmp_path / "h.h2"), str(tmp_path / "d.h2")
+    H.save(fa)
+    D.save(fb)
+    a, b = open(fa, "rb").read(), open(fb, "rb").read()
+    assert len(a) == len(b) and a[:60] == b[:60] and a[92:-8] == b[92:-8]
