@@ -176,7 +176,12 @@ def _stream_ptr(stream):
 
 
 class H2Matrix:
-    """A compressed kernel matrix K~ (H2*(b+t), (H2+H)* or H2_sqrt(d)(b))."""
+    """A compressed kernel matrix K~ (H2*(b+t), (H2+H)* or H2_sqrt(d)(b)).
+
+    `pivots`: where the ACA pivot search of the construction runs -- None (the
+    device for 1/r and the IMQ unless host_only, else the host), "device" or
+    "host"; the device search takes the host's decisions (h2_build_opts.pivots).
+    """
 
     def __init__(self, points, kernel, leaf_size=64, tol=1e-8, variant="h2star", storage="f64",
                  eps_far=None, eps_ver=None, kappa=None, domain=None, threads=0,
