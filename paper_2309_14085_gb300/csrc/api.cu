@@ -422,17 +422,21 @@ std::vector<Tile> row_tiles(h2_handle h, int nrhs) {
     return t;
 }
 
-// Autotuner: for the two large block-row lists (M2L and the stored leaf rows)
-// time 2, 4 and 8 rows per warp on the device (the coefficient buffer is
-// scratch here): the fastest of 5 individually timed launches per width; 4
-// rows stays unless another width is more than 3 % faster.  Small lists use 4.
+// Autotuner: for every block-row list of the single-RHS product (M2L, the
+// stored leaf rows, P2M and each M2M and L2L level) time 2, 4 and 8 rows per
+// warp on the device (the coefficient buffer is scratch here): the fastest of
+// 5 individually timed launches per width; 4 rows stays unless another width
+// is more than 3 % faster.  The width only decides which rows a warp takes, so
+// every choice gives the same results bit for bit.
 template <class A>
 int autotune(h2_handle h) {
     cudaEvent_t ev[6];
     for (auto& e : ev) H2_CUDA(cudaEventCreate(&e));
-    DevRowTasks* lists[2] = {&h->m2l, &h->leaf};
+    std::vector<DevRowTasks*> lists = {&h->m2l, &h->leaf, &h->p2m};
+    for (DevRowTasks& R : h->m2m) lists.push_back(&R);
+    for (DevRowTasks& R : h->l2l) lists.push_back(&R);
     const int rws[3] = {2, 4, 8};
-    for (int li = 0; li < 2; ++li) {
+    for (size_t li = 0; li < lists.size(); ++li) {
         DevRowTasks& R = *lists[li];
         if (R.n == 0 || (li == 0 && h->host.m2l_fly)) continue;   // no stored M2L blocks
         double t[3];
@@ -452,7 +456,7 @@ int autotune(h2_handle h) {
                 best = std::min(best, double(ms));
             }
             t[k] = best;
-            h->tune_ms[li][k] = best;
+            if (li < 2) h->tune_ms[li][k] = best;
         }
         int pick = 1;                       // 4 rows per warp
         for (int k = 0; k < 3; ++k)
