@@ -457,3 +457,23 @@ def test_b2t_over_the_weak_admissibility_loses_accuracy_and_t2b_does_not():
     assert re["h2star"] <= 100 * eps
     assert re["h2star_b"] >= 1e4 * re["h2star_t"]
     assert re["h2star_b"] >= 1e3 * re["h2star"]
+
+
+def test_log_and_exp_are_the_c_librarys():
+    """Reading of the kernels' elementary functions: log r and exp(-r) are the
+    platform C library's, entry by entry (Python's math.log / math.exp call
+    that library), so ACA ties on tensor grids break on the same values as in
+    any C or C++ construction built on it; the other kernels use only IEEE
+    operations.  A vectorised exp (numpy's on x86) differs from the C
+    library's in the last bit on a few percent of these arguments, which would
+    fail the equality below."""
+    r = np.random.default_rng(97).uniform(1e-3, 4.0, 20000)
+    assert np.array_equal(kernels.G("log2d", r), np.array([math.log(x) for x in r]))
+    assert np.array_equal(kernels.G("matern12", r), np.array([math.exp(-x) for x in r]))
+    P = inputs.chebyshev_grid(6, 2)
+    B = kernels.block("matern12", P, np.arange(36), np.arange(36))
+    for i in range(36):
+        for j in range(36):
+            dx, dy = P[i, 0] - P[j, 0], P[i, 1] - P[j, 1]
+            want = 1.0 if i == j else math.exp(-math.sqrt(dx * dx + dy * dy))
+            assert B[i, j] == want
