@@ -83,7 +83,11 @@ typedef struct {
     double eps_ver;        /* tolerance for vertex-sharing clusters (default: tol)     */
     int    storage;        /* H2_F64 (default), H2_F32, H2_DF64 or H2_BF16             */
     int    kappa;          /* leaf level; 0 = smallest kappa with leaf_size 2^(d kappa) >= N
-                              (§3.1); a positive value forces that depth           */
+                              (§3.1); a positive value forces that depth; -1 = the
+                              strict reading of §3.1: from that depth on, the first
+                              at which every leaf holds at most leaf_size points
+                              (H2_E_INVALID_ARG if none up to 2^24 leaves does,
+                              e.g. more than leaf_size coincident points)         */
     int    use_domain;     /* 1: use domain_lo / domain_side as the root hyper-cube C  */
     double domain_lo[3];   /*    lower corner of C                                    */
     double domain_side;    /*    edge length of C; default C = tight bounding cube    */

@@ -4,7 +4,8 @@ Tree (§3.1): level 0 is the hyper-cube C; every box of level l splits into
 2^d boxes of level l+1; the leaves sit at level kappa with
 kappa = ceil(log_{2^d}(N / n_max)) -- the smallest kappa with
 n_max * 2^(d kappa) >= N (reading: the formula of §3.1, not "deepen until every
-leaf holds <= n_max points").
+leaf holds <= n_max points"; that other reading is available as
+kappa="strict", `kappa_strict`).
 
 Reading of the domain C (§3.1 only asks for a compact hyper-cube holding the
 points): the tight bounding cube, lo_k = min_i x_ik and side = max_k
@@ -51,6 +52,25 @@ def kappa_formula(N, n_max, d):
     return k
 
 
+def kappa_strict(P, n_max, lo, side, cap=20):
+    """The other reading of §3.1's stopping rule ("subdivide until every leaf
+    holds at most n_max points"): the smallest kappa, from the formula's up,
+    at which every leaf box of the uniform tree holds at most n_max points.
+    Raises ValueError when kappa would exceed `cap` (more than n_max points
+    that no box size separates, e.g. coincident points)."""
+    P = np.asarray(P, dtype=np.float64)
+    N, d = P.shape
+    k = kappa_formula(N, n_max, d)
+    while True:
+        c = np.clip(np.floor((P - lo) / side * float(1 << k)).astype(np.int64), 0, (1 << k) - 1)
+        _, counts = np.unique(c, axis=0, return_counts=True)
+        if counts.max() <= n_max:
+            return k
+        k += 1
+        if k > cap:
+            raise ValueError("no tree depth up to %d separates the points into leaves of %d" % (cap, n_max))
+
+
 def bounding_cube(P):
     lo = P.min(axis=0)
     side = float((P.max(axis=0) - lo).max())
@@ -94,9 +114,14 @@ class Tree:
         P = np.asarray(P, dtype=np.float64)
         self.P = P
         self.N, self.d = P.shape
-        self.kappa = kappa_formula(self.N, n_max, self.d) if kappa is None else int(kappa)
         self.lo, self.side = bounding_cube(P) if domain is None else domain
         self.lo = np.asarray(self.lo, dtype=np.float64)
+        if kappa is None:
+            self.kappa = kappa_formula(self.N, n_max, self.d)
+        elif kappa == "strict":
+            self.kappa = kappa_strict(P, n_max, self.lo, self.side)
+        else:
+            self.kappa = int(kappa)
         scale = float(1 << self.kappa)
         c = np.floor((P - self.lo) / self.side * scale).astype(np.int64)
         self.leaf_coords = np.clip(c, 0, (1 << self.kappa) - 1)

@@ -196,7 +196,7 @@ class H2Matrix:
         o.eps_far = eps_far or 0.0
         o.eps_ver = eps_ver or 0.0
         o.storage = STORAGE[storage]
-        o.kappa = kappa or 0
+        o.kappa = -1 if kappa == "strict" else (kappa or 0)
         if domain is not None:
             lo, side = domain
             o.use_domain = 1

@@ -978,7 +978,7 @@ int h2_build(const double* points, int64_t N, int d, int kernel, int leaf_size, 
     if (o.pivots < 0 || o.pivots > 2) return fail(H2_E_INVALID_ARG, "pivots must be 0, 1 or 2");
     if (o.pivots == 1 && o.host_only)
         return fail(H2_E_INVALID_ARG, "the device pivot search needs a device (host_only set)");
-    if (o.kappa < 0 || o.kappa > 20) return fail(H2_E_INVALID_ARG, "kappa out of range");
+    if (o.kappa < -1 || o.kappa > 20) return fail(H2_E_INVALID_ARG, "kappa out of range");
     if (o.eps_far < 0 || o.eps_far >= 1 || o.eps_ver < 0 || o.eps_ver >= 1)
         return fail(H2_E_INVALID_ARG, "eps_far / eps_ver must be in [0, 1)");
     if (o.use_domain && !(o.domain_side > 0)) return fail(H2_E_INVALID_ARG, "domain_side must be > 0");

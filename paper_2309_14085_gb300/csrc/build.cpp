@@ -50,8 +50,12 @@ int classify(const int* a, const int* b, int d) {
 
 // ---------------------------------------------------------------------------
 // Tree (§3.1)
-void build_tree(Tree& t, const double* P, int64_t N, int d, int leaf_size, int kappa_forced,
-                const double* dom_lo, double dom_side) {
+// deepest tree the strict depth rule may reach
+constexpr int kKappaCap = 20;
+
+// Returns "" or an error message (the strict depth rule found no separating depth).
+std::string build_tree(Tree& t, const double* P, int64_t N, int d, int leaf_size, int kappa_forced,
+                       const double* dom_lo, double dom_side) {
     t.N = N;
     t.d = d;
     if (kappa_forced > 0) {
@@ -75,6 +79,33 @@ void build_tree(Tree& t, const double* P, int64_t N, int d, int leaf_size, int k
         double s = 0.0;
         for (int k = 0; k < d; ++k) s = std::max(s, hi[k] - t.lo[k]);
         t.side = s > 0.0 ? s : 1.0;
+    }
+    if (kappa_forced < 0) {
+        // the strict reading of §3.1: from the formula's depth, deepen until
+        // every leaf box holds at most leaf_size points
+        for (;; ++t.kappa) {
+            if (t.kappa > kKappaCap || int64_t(1) << (d * t.kappa) > (int64_t(1) << 24))
+                return "no tree depth up to 2^24 leaves separates the points into leaves of leaf_size";
+            const double sc = double(int64_t(1) << t.kappa);
+            const int cm = (1 << t.kappa) - 1;
+            std::vector<int64_t> keys(N);
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < N; ++i) {
+                int c[3];
+                for (int k = 0; k < d; ++k) {
+                    const double f = std::floor((P[i * d + k] - t.lo[k]) / t.side * sc);
+                    c[k] = f < 0.0 ? 0 : (f > double(cm) ? cm : int(f));
+                }
+                keys[i] = morton(c, t.kappa, d);
+            }
+            std::sort(keys.begin(), keys.end());
+            int64_t run = 0, worst = 0;
+            for (int64_t i = 0; i < N; ++i) {
+                run = (i > 0 && keys[i] == keys[i - 1]) ? run + 1 : 1;
+                worst = std::max(worst, run);
+            }
+            if (worst <= leaf_size) break;
+        }
     }
     const double scale = double(int64_t(1) << t.kappa);
     const int cmax = (1 << t.kappa) - 1;
@@ -100,6 +131,7 @@ void build_tree(Tree& t, const double* P, int64_t N, int d, int leaf_size, int k
     t.x.resize(size_t(N) * d);
     for (int64_t i = 0; i < N; ++i)
         for (int k = 0; k < d; ++k) t.x[i * d + k] = P[t.perm[i] * d + k];
+    return "";
 }
 
 // ---------------------------------------------------------------------------
@@ -1120,7 +1152,11 @@ std::string build_host(Host& H, const double* points, int64_t N, int d, int leaf
         explicit ThreadCount(int n) : prev(omp_get_max_threads()) { if (n > 0) omp_set_num_threads(n); }
         ~ThreadCount() { omp_set_num_threads(prev); }
     } thread_count(threads);
-    build_tree(H.tree, points, N, d, leaf_size, kappa_forced, domain_lo, domain_side);
+    {
+        const std::string e = build_tree(H.tree, points, N, d, leaf_size, kappa_forced, domain_lo,
+                                         domain_side);
+        if (!e.empty()) return e;
+    }
     if (H.tree.kappa > 20 / (d == 2 ? 1 : 1) || H.tree.nboxes(H.tree.kappa) > (int64_t(1) << 24))
         return "tree too deep (more than 2^24 leaves)";
     tick("tree");

@@ -284,3 +284,26 @@ def test_degenerate_trees_build():
     P = inputs.points(500, 3, 5, lo=0.0, hi=0.2)
     D = H2Matrix(P, "invr", leaf_size=8, tol=1e-6, domain=((0.0, 0.0, 0.0), 1.0), host_only=True)
     assert D.info()["kappa"] >= 2
+
+
+@pytest.mark.parametrize("kind,d", [("log2d", 2), ("invr", 3)])
+def test_strict_tree_depth_matches_oracle(kind, d):
+    """kappa = -1 (the strict reading of §3.1) on clustered points: the same
+    depth, tree order and B2T / T2B pivots as the oracle's strict tree; more
+    coincident points than leaf_size are refused."""
+    nu, nc, side = (1500, 300, 0.3) if d == 2 else (1850, 150, 0.5)
+    P = np.vstack([inputs.points(nu, d, 801 + d), inputs.points(nc, d, 811 + d, lo=0.0, hi=side)])
+    A = H2Matrix(P, kind, leaf_size=32, tol=1e-6, kappa="strict", host_only=True)
+    O = oh2.H2(P, kind, n_max=32, eps=1e-6, kappa="strict")
+    assert A.info()["kappa"] == O.tree.kappa == (5 if d == 2 else 3)
+    assert np.array_equal(A.tree_order(), O.tree.order)
+    for b, name in enumerate(["far", "ver"]):
+        B = O.bases[name]
+        for (l, X), ti in B.ti.items():
+            gti, gsi = A.pivots(b, l, X)
+            assert np.array_equal(gti, ti), (name, l, X)
+            assert np.array_equal(gsi, B.si[(l, X)]), (name, l, X)
+    with pytest.raises(H2Error) as e:
+        H2Matrix(np.repeat(inputs.points(4, d, 5), 40, axis=0), kind, leaf_size=32, tol=1e-6,
+                 kappa="strict", host_only=True)
+    assert e.value.code == -1

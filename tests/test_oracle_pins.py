@@ -477,3 +477,38 @@ def test_log_and_exp_are_the_c_librarys():
             dx, dy = P[i, 0] - P[j, 0], P[i, 1] - P[j, 1]
             want = 1.0 if i == j else math.exp(-math.sqrt(dx * dx + dy * dy))
             assert B[i, j] == want
+
+
+def _clustered(d):
+    """Uniform points in [-1, 1]^d plus a denser cluster in [0, side]^d (2D:
+    1500 + 300 in side 0.3, strict depth 5 against the formula's 3; 3D: 1850 +
+    150 in side 0.5, depth 3 against 2)."""
+    nu, nc, side = (1500, 300, 0.3) if d == 2 else (1850, 150, 0.5)
+    return np.vstack([inputs.points(nu, d, 801 + d), inputs.points(nc, d, 811 + d, lo=0.0, hi=side)])
+
+
+def _max_occupancy(P, lo, side, k):
+    c = np.clip(np.floor((P - lo) / side * float(1 << k)).astype(np.int64), 0, (1 << k) - 1)
+    return int(np.unique(c, axis=0, return_counts=True)[1].max())
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_strict_tree_depth_is_the_smallest_that_separates(d):
+    """The strict reading of §3.1 (subdivide until every leaf holds at most
+    n_max points): the depth holds every leaf to n_max, one level less does
+    not (or it is the formula's depth), and on uniform points that the formula
+    already separates it equals the formula's depth.  Coincident points beyond
+    n_max have no such depth."""
+    n_max = 32
+    P = _clustered(d)
+    T = tree.Tree(P, n_max=n_max, kappa="strict")
+    k0 = tree.kappa_formula(P.shape[0], n_max, d)
+    assert T.kappa > k0
+    assert _max_occupancy(P, T.lo, T.side, T.kappa) <= n_max
+    assert _max_occupancy(P, T.lo, T.side, T.kappa - 1) > n_max
+    assert int(np.bincount(T.leaf_key).max()) <= n_max
+    G = inputs.uniform_grid(8, d)           # 8^d points, one per box of an 8^d grid
+    TG = tree.Tree(G, n_max=1, kappa="strict")
+    assert TG.kappa == tree.kappa_formula(G.shape[0], 1, d) == 3
+    with pytest.raises(ValueError):
+        tree.Tree(np.repeat(inputs.points(4, d, 5), 40, axis=0), n_max=32, kappa="strict")
