@@ -65,12 +65,15 @@ def _degenerate():
     yield H2Matrix(Q, "imq", leaf_size=8, tol=1e-8, variant="h2plush", host_only=True)
     yield H2Matrix(inputs.points(700, 3, 7), "matern12", leaf_size=16, tol=1e-6,
                    variant="h2sqrt", near="stored", storage="f32", host_only=True)
+    C = np.vstack([inputs.points(1500, 2, 803), inputs.points(300, 2, 813, lo=0.0, hi=0.3)])
+    yield H2Matrix(C, "invr", leaf_size=32, tol=1e-6, kappa="strict", host_only=True)  # depth 5
 
 
 def test_degenerate_constructions_round_trip(tmp_path):
     """The loaded-state checks accept every layout the construction makes,
     including one leaf, one point, no far field, empty boxes, coincident
-    points (each file is also written again byte for byte)."""
+    points and a strict-depth tree over clustered points (each file is also
+    written again byte for byte)."""
     for k, A in enumerate(_degenerate()):
         f1, f2 = str(tmp_path / f"{k}a.h2"), str(tmp_path / f"{k}b.h2")
         A.save(f1)
