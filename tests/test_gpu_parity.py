@@ -296,3 +296,19 @@ def test_fp64_near_field_on_the_fly_in_double_float(kind, nrhs):
     ref = h2.H2(P, kind, n_max=48, eps=1e-8, param=kw.get("kparam", 0.1)).matvec(Q).reshape(N, nrhs)
     print(f"df near {kind} nrhs {nrhs}: vs oracle {_maxrel(y, ref):.2e}, vs stored {_maxrel(y, z):.2e}")
     assert _maxrel(y, ref) <= F64_TOL and _maxrel(y, z) <= F64_TOL
+
+
+def test_strict_depth_tree_matches_oracle():
+    """A strict-depth tree (the other reading of §3.1: subdivide until every
+    leaf holds at most n_max points) over clustered points: depth 5 where the
+    formula gives 3, with many nearly empty leaves.  fp64 bar against the
+    oracle's own strict construction, dense bar as elsewhere."""
+    P = np.vstack([inputs.points(1500, 2, 803), inputs.points(300, 2, 813, lo=0.0, hi=0.3)])
+    q = inputs.rhs(P.shape[0], 1, 823)
+    A = H2Matrix(P, "log2d", leaf_size=32, tol=1e-8, kappa="strict")
+    assert A.info()["kappa"] == 5
+    y = _gpu_mvp(A, q)
+    O = h2.H2(P, "log2d", n_max=32, eps=1e-8, kappa="strict")
+    ref = O.matvec(q)
+    assert _maxrel(y, ref) <= F64_TOL
+    _dense_bar(y, ref, dense.product("log2d", P, q), 1e-8)
