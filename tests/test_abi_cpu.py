@@ -307,3 +307,31 @@ def test_strict_tree_depth_matches_oracle(kind, d):
         H2Matrix(np.repeat(inputs.points(4, d, 5), 40, axis=0), kind, leaf_size=32, tol=1e-6,
                  kappa="strict", host_only=True)
     assert e.value.code == -1
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/h2star.h is a C header: a C99 program compiles against it with
+    -pedantic -Werror, links against the library and gets INVALID_ARG and a
+    message from h2_build with no points (no device is touched)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "h2star.h"\n'
+        "int main(void) {\n"
+        "    h2_build_opts o = {0};\n"
+        "    h2_handle h = 0;\n"
+        "    int rc = h2_build(0, 10, 2, H2_KERNEL_LOG2D, 8, 1e-6, H2_STAR_BT, &o, &h);\n"
+        '    printf("%d %s\\n", rc, h2_last_error());\n'
+        "    return rc == H2_E_INVALID_ARG && h == 0 ? 0 : 1;\n"
+        "}\n")
+    exe = tmp_path / "abi"
+    lib_dir = os.path.dirname(pkg.lib()._name)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L" + lib_dir, "-lh2star", "-Wl,-rpath," + lib_dir], check=True)
+    out = subprocess.run([str(exe)], stdout=subprocess.PIPE, text=True)
+    assert out.returncode == 0, out.stdout
+    assert out.stdout.startswith("-1 ") and len(out.stdout.strip()) > 3
